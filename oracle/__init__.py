@@ -1,0 +1,188 @@
+"""CPU oracle for the short-range P3M force -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The product library never calls, links or loads
+it.  The C source (``oracle.c``) is a plain FP64 restatement of the paper's
+short-range sum (Section 2.1.3, Eq. p3m_gravity), the rung rule (Eq. rung) and
+the kick/drift operators (Section 2.2.2).
+
+Parity pins (each checked by a ``-m "not gpu"`` test):
+  * bracket B(r) against the gradient of the Ewald short-range potential
+    erfc(r/2x_s)/r and Gauss's law for the softening shapes (mpmath);
+  * cell-list sum against O(N^2) brute force, and against an explicit sum over
+    the 27 nearest periodic images;
+  * Newton's third law, permutation and translation invariance;
+  * VJP against central finite differences of the oracle's own forward;
+  * rungs against the log2/ceil definition; subtile ids against floor().
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SOFTENING = {"none": 0, "plummer": 1, "bspline": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _oracle.so (gcc, OpenMP, no FP contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, d, p, i = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
+            lib.oracle_bracket.argtypes = [d, d, i, d]
+            lib.oracle_bracket.restype = d
+            lib.oracle_bracket_dr.argtypes = [d, d, i, d]
+            lib.oracle_bracket_dr.restype = d
+            common = [d, d, d, d, i, d]
+            lib.oracle_sr_accel.argtypes = [i64, p, p, i] + common + [p]
+            lib.oracle_sr_accel.restype = i64
+            lib.oracle_sr_accel_brute.argtypes = [i64, p, p, i] + common + [p]
+            lib.oracle_sr_accel_brute.restype = i64
+            lib.oracle_sr_accel_subset.argtypes = [i64, p, i64, p] + common + [p, p]
+            lib.oracle_sr_accel_subset.restype = i64
+            lib.oracle_sr_vjp.argtypes = [i64, p, p, i] + common + [p, p]
+            lib.oracle_sr_vjp.restype = i64
+            lib.oracle_subtile_ids.argtypes = [i64, p, i, i, p]
+            lib.oracle_subtile_ids.restype = None
+            lib.oracle_rungs.argtypes = [i64, p, d, d, d, i, p]
+            lib.oracle_rungs.restype = i64
+            lib.oracle_kick.argtypes = [i64, p, p, p, i, p]
+            lib.oracle_kick.restype = None
+            lib.oracle_drift.argtypes = [i64, p, p, d, d]
+            lib.oracle_drift.restype = None
+            lib.oracle_num_threads.argtypes = []
+            lib.oracle_num_threads.restype = i
+            _lib = lib
+    return _lib
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _soft(s):
+    return SOFTENING[s] if isinstance(s, str) else int(s)
+
+
+def num_threads() -> int:
+    return _load().oracle_num_threads()
+
+
+def bracket(r, x_s, softening="bspline", eps=0.0):
+    """B(r) of Eq. p3m_gravity (without -G m), vectorised over r."""
+    lib = _load()
+    r = np.atleast_1d(np.asarray(r, dtype=np.float64))
+    return np.array([lib.oracle_bracket(float(v), x_s, _soft(softening), eps) for v in r])
+
+
+def bracket_dr(r, x_s, softening="bspline", eps=0.0):
+    lib = _load()
+    r = np.atleast_1d(np.asarray(r, dtype=np.float64))
+    return np.array([lib.oracle_bracket_dr(float(v), x_s, _soft(softening), eps) for v in r])
+
+
+def _rung_arg(rung):
+    if rung is None:
+        return None
+    return np.ascontiguousarray(rung, dtype=np.int8)
+
+
+def sr_accel(pos, x_s, x_r, G_m, softening="bspline", eps=0.0, rung=None, rung_min=0, box=1.0,
+             out=None, brute=False):
+    """Short-range accelerations (3, N) and the interacting-pair count.
+
+    Rows of inactive receivers (rung < rung_min) are left as in ``out``
+    (zeros by default)."""
+    pos = _f64(pos)
+    n = pos.shape[1]
+    acc = np.zeros((3, n)) if out is None else out
+    rg = _rung_arg(rung)
+    fn = _load().oracle_sr_accel_brute if brute else _load().oracle_sr_accel
+    pairs = fn(n, _ptr(pos), _ptr(rg), rung_min, box, x_s, x_r, G_m, _soft(softening), eps, _ptr(acc))
+    if pairs < 0:
+        raise ValueError("oracle: fewer than 3 cells per dimension (x_r too large for the box)")
+    return acc, int(pairs)
+
+
+def sr_accel_subset(pos, receivers, x_s, x_r, G_m, softening="bspline", eps=0.0, box=1.0):
+    """Accelerations (3, n_sub) of the listed receivers and per-receiver pair counts."""
+    pos = _f64(pos)
+    n = pos.shape[1]
+    recv = np.ascontiguousarray(receivers, dtype=np.int64)
+    acc = np.zeros((3, len(recv)))
+    pairs = np.zeros(len(recv), dtype=np.int64)
+    tot = _load().oracle_sr_accel_subset(n, _ptr(pos), len(recv), _ptr(recv), box, x_s, x_r, G_m,
+                                         _soft(softening), eps, _ptr(acc), _ptr(pairs))
+    if tot < 0:
+        raise ValueError("oracle: bad geometry")
+    return acc, pairs
+
+
+def sr_vjp(pos, abar, x_s, x_r, G_m, softening="bspline", eps=0.0, rung=None, rung_min=0, box=1.0):
+    """xbar = (d a / d x)^T abar over all particles, (3, N)."""
+    pos = _f64(pos)
+    abar = _f64(abar)
+    n = pos.shape[1]
+    xbar = np.zeros((3, n))
+    rg = _rung_arg(rung)
+    tot = _load().oracle_sr_vjp(n, _ptr(pos), _ptr(rg), rung_min, box, x_s, x_r, G_m, _soft(softening),
+                                eps, _ptr(abar), _ptr(xbar))
+    if tot < 0:
+        raise ValueError("oracle: bad geometry")
+    return xbar
+
+
+def subtile_ids(pos, n_tile, n_sub):
+    pos = _f64(pos)
+    n = pos.shape[1]
+    ids = np.empty(n, dtype=np.int32)
+    _load().oracle_subtile_ids(n, _ptr(pos), n_tile, n_sub, _ptr(ids))
+    return ids
+
+
+def rungs(acc, dt, eta, eps, n_rung=8):
+    acc = _f64(acc)
+    n = acc.shape[1]
+    out = np.empty(n, dtype=np.int8)
+    bad = _load().oracle_rungs(n, _ptr(acc), dt, eta, eps, n_rung, _ptr(out))
+    return out, int(bad)
+
+
+def kick(mom, acc, kick_factor, rung=None, rung_min=0):
+    mom = _f64(mom).copy()
+    acc = _f64(acc)
+    kf = np.ascontiguousarray(kick_factor, dtype=np.float64)
+    _load().oracle_kick(mom.shape[1], _ptr(mom), _ptr(acc), _ptr(_rung_arg(rung)), rung_min, _ptr(kf))
+    return mom
+
+
+def drift(pos, mom, factor, box=1.0):
+    pos = _f64(pos).copy()
+    mom = _f64(mom)
+    _load().oracle_drift(pos.shape[1], _ptr(pos), _ptr(mom), factor, box)
+    return pos
