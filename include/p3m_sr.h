@@ -1,0 +1,216 @@
+/*
+ * p3m_sr.h -- C ABI of the GB300 short-range P3M gravity library.
+ *
+ * The library computes the short-range half of CONCEPT 1.0's P3M gravity
+ * (arXiv:2112.01508, Section 2.1.3, lower half of Eq. p3m_gravity):
+ *
+ *   a_i = -G m  sum_{j != i, |x_ij| < x_r}  B(|x_ij|) x_ij ,
+ *   B(r) = erfc(u)/r^3 + exp(-u^2)/(sqrt(pi) x_s r^2) + ( |x|^{-3}_shape - r^{-3} ),
+ *   u = r/(2 x_s),  x_ij = nearest periodic image of x_i - x_j,
+ *
+ * over the paper's tile/subtile decomposition of the periodic box (Section
+ * 2.1.3, "Tiles" and "Subtiles"), for the receivers on the active rungs of the
+ * individual time-stepping (Section 2.2.2), plus the rung rule (Eq. rung), the
+ * kick and drift operators (Section 2.2.2) and the vector-Jacobian product of
+ * the accelerations with respect to positions.
+ *
+ * Conventions shared by every entry point:
+ *   - Particle arrays are DEVICE pointers owned by the caller (for example the
+ *     data_ptr of torch tensors).  Vectors are structure-of-arrays, 3 x n:
+ *     x[0..n), then y[0..n), then z[0..n).  The library never frees them.
+ *   - The context owns its scratch memory (sort buffers, offsets, chunk lists),
+ *     allocated once by p3m_sr_create for the particle count given there.
+ *   - Every call only enqueues work on the context's CUDA stream and returns
+ *     without synchronising (except p3m_sr_sync and p3m_sr_stats).
+ *   - Errors are returned, never aborted on.  Argument errors are detected on
+ *     the host and returned immediately.  Errors found by kernels (non-finite
+ *     or out-of-box positions, non-finite accelerations) are latched in a
+ *     device word; p3m_sr_sync waits for the stream and returns the latched
+ *     status, and later calls return it once the copy that reports it has
+ *     landed.  p3m_sr_last_error gives a human-readable message.
+ *   - "precision" arguments are 32 (float) or 64 (double).
+ *   - After p3m_sr_sort, every other call assumes the particles are in the
+ *     sorted (tile -> subtile -> particle) order and positions lie in [0, L).
+ */
+#ifndef P3M_SR_H
+#define P3M_SR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  P3M_OK = 0,
+  P3M_ERR_INVALID = 1,        /* bad argument or parameter                          */
+  P3M_ERR_TOO_FEW_TILES = 2,  /* fewer than 4 tiles per dimension (Section 2.1.3)   */
+  P3M_ERR_OOM = 3,            /* device allocation failed                           */
+  P3M_ERR_CUDA = 4,           /* a CUDA runtime call failed                         */
+  P3M_ERR_TIMEOUT = 5,        /* reserved: a bounded device-side wait expired       */
+  P3M_ERR_NONFINITE = 6,      /* non-finite or out-of-box input met by a kernel     */
+  P3M_ERR_STATE = 7           /* call out of order (e.g. forces before sort)        */
+} p3m_status;
+
+typedef enum { P3M_SOFT_NONE = 0, P3M_SOFT_PLUMMER = 1, P3M_SOFT_BSPLINE = 2 } p3m_softening;
+
+/*
+ * Physical and decomposition parameters.
+ *   n          number of particles (0 <= n < 2^31)
+ *   box        periodic box side L (> 0)
+ *   x_s, x_r   force split scale and cutoff, 0 < x_s, 0 < x_r <= L/4
+ *              (paper defaults x_s = 1.25 L/n_phi, x_r = 4.5 x_s, Eq. p3m_parameters)
+ *   G_m        G times the particle mass (accelerations are returned)
+ *   softening  p3m_softening: none, Plummer (Eq. plummer_shape) or B-spline
+ *              (Eq. bspline_force with eps_B = 2.8 eps, Section 2.1.1)
+ *   eps        Plummer softening length epsilon (> 0 when softened)
+ *   n_sub      subtiles per tile along x, y, z (each 1..16)
+ *   n_rung     number of rungs, 1..8 (Section 2.2.2)
+ * The box is split into n_t = floor(L / x_r) tiles per dimension (tiles are at
+ * least x_r wide, Section 2.1.3); n_t must be at least 4.
+ */
+typedef struct {
+  int64_t n;
+  double box;
+  double x_s;
+  double x_r;
+  double G_m;
+  int softening;
+  double eps;
+  int n_sub[3];
+  int n_rung;
+} p3m_sr_params;
+
+typedef struct p3m_sr_ctx p3m_sr_ctx;
+
+/* Geometry and counters, filled by p3m_sr_stats. */
+typedef struct {
+  int n_tile;              /* tiles per dimension                               */
+  int n_sub[3];            /* subtiles per tile per dimension                   */
+  int64_t n_subtiles;      /* (n_tile n_sub[0]) (n_tile n_sub[1]) (n_tile n_sub[2]) */
+  int64_t n_active;        /* receivers of the last p3m_sr_build_pairs          */
+  int64_t n_chunks;        /* receiver chunks (<= 32 particles) of that call    */
+  int64_t pairs_last;      /* interacting ordered pairs (i active, j != i,
+                              r^2 < x_r^2) met by the last forces/vjp call      */
+  int64_t kernel_launches; /* kernels launched by this context so far           */
+  double force_kernel_ms;  /* device time of the last forward pair kernel       */
+  double vjp_kernel_ms;    /* device time of the last adjoint pair kernel       */
+} p3m_sr_stats_t;
+
+/*
+ * Create a context for n particles.  cuda_stream is a cudaStream_t (NULL: the
+ * legacy default stream).  Validates the parameters (P3M_ERR_INVALID,
+ * P3M_ERR_TOO_FEW_TILES) and allocates all scratch on the current device
+ * (P3M_ERR_OOM).  *out is NULL on failure.
+ */
+p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stream, p3m_sr_ctx** out);
+
+/* Free the context and its scratch.  NULL is ignored. */
+void p3m_sr_destroy(p3m_sr_ctx* ctx);
+
+/* Message describing the last error of this context (never NULL). */
+const char* p3m_sr_last_error(const p3m_sr_ctx* ctx);
+
+/* Wait for the context's stream; return the latched device status. */
+p3m_status p3m_sr_sync(p3m_sr_ctx* ctx);
+
+/* Synchronise and fill *out (see p3m_sr_stats_t). */
+p3m_status p3m_sr_stats(p3m_sr_ctx* ctx, p3m_sr_stats_t* out);
+
+/*
+ * Sort the particles into tiles and subtiles (Section 2.1.3: O(N) sort into
+ * tiles, memory reordered in tile -> subtile -> particle walk order).
+ *   pos          3 x n float64 SoA, device; reordered IN PLACE.  Each position
+ *                must be finite and in [0, L) (else P3M_ERR_NONFINITE is
+ *                latched and the particle is binned at the clamped cell).
+ *   carry        n_carry device arrays of n elements of carry_bytes[c] bytes
+ *                each (1..32), permuted in place alongside (momenta, rungs,
+ *                identifiers ...).  May be NULL when n_carry == 0.
+ *   perm_out     nullable, n int32: perm_out[k] = pre-sort index of the
+ *                particle now at k.
+ *   subtile_id_out nullable, n int32: subtile id of the particle now at k.
+ * Subtile of a particle: g_d = min(floor(x_d * (M_d / L)), M_d - 1) with
+ * M_d = n_t n_sub[d] (one correctly rounded multiply), tile t_d = g_d / n_sub[d],
+ * s_d = g_d mod n_sub[d];
+ *   id = ((t_x n_t + t_y) n_t + t_z) (n_sub[0] n_sub[1] n_sub[2]) + (s_x n_sub[1] + s_y) n_sub[2] + s_z.
+ * The sort is stable (equal ids keep their input order) and deterministic.
+ */
+p3m_status p3m_sr_sort(p3m_sr_ctx* ctx, double* pos, void* const* carry, const int* carry_bytes,
+                       int n_carry, int32_t* perm_out, int32_t* subtile_id_out);
+
+/*
+ * Build the receiver set and work list for the following forces / vjp calls
+ * (Section 2.1.3 "precomputed (sub)tile pairings"; Section 2.2.2: receivers are
+ * the particles on rungs >= rung_min, suppliers are all particles).
+ *   rung      nullable device int8 array (sorted order); NULL: all active.
+ *   rung_min  current rung; particles with rung >= rung_min are receivers.
+ * Must follow p3m_sr_sort (P3M_ERR_STATE otherwise).
+ */
+p3m_status p3m_sr_build_pairs(p3m_sr_ctx* ctx, const int8_t* rung, int rung_min);
+
+/*
+ * Short-range accelerations (Section 2.1.3, short-range half of Eq.
+ * p3m_gravity) on the receivers of the last p3m_sr_build_pairs.
+ *   pos        3 x n float64 SoA, device, in the sorted order.
+ *   precision  32: FP32 arithmetic and accumulation, displacements taken
+ *              relative to subtile origins (positions read once in FP64);
+ *              acc_out is 3 x n float.  64: FP64 throughout, acc_out 3 x n
+ *              double.
+ *   acc_out    receivers' rows are overwritten; other rows are untouched.
+ * The FP32 path requires x_r <= 4.6 x_s (range of its erfc fit).
+ */
+p3m_status p3m_sr_forces(p3m_sr_ctx* ctx, const double* pos, int precision, void* acc_out);
+
+/*
+ * Rungs from accelerations (Section 2.2.2, Eq. rung):
+ *   l_i = max(0, ceil(log2(dt sqrt(|a_i| / (2 eta eps))))), clamped to n_rung-1,
+ * evaluated exactly as: q = dt*dt / ((2*eta)*eps); s = (q*q) * ((ax*ax + ay*ay) + az*az);
+ * l = smallest l >= 0 with s <= 16^l (IEEE double, correctly rounded, no FMA).
+ *   acc        3 x n SoA device, acc_precision 32 or 64 (floats are widened).
+ *   rung_out   n int8 device.
+ * Non-finite accelerations get rung 0 and latch P3M_ERR_NONFINITE.
+ */
+p3m_status p3m_sr_assign_rungs(p3m_sr_ctx* ctx, const void* acc, int acc_precision, double dt,
+                               double eta, double eps, int8_t* rung_out);
+
+/*
+ * Kick (Section 2.2.2, operator K with a = 1): for particles with
+ * rung >= rung_min (all when rung is NULL, using kick_factor[0]),
+ *   q_i <- q_i + a_i * kick_factor[rung_i]     in double (widen, multiply, add).
+ *   mom        3 x n device, mom_precision 32 or 64 (FP32 momenta are rounded
+ *              once after the double update).
+ *   acc        3 x n device, acc_precision 32 or 64.
+ *   kick_factor HOST array of n_rung doubles (K(Delta t / 2^l)).
+ */
+p3m_status p3m_sr_kick(p3m_sr_ctx* ctx, void* mom, int mom_precision, const void* acc,
+                       int acc_precision, const int8_t* rung, int rung_min,
+                       const double* kick_factor);
+
+/*
+ * Drift (Section 2.2.2, operator D with a = 1):
+ *   x_i <- x_i + q_i * factor, then wrapped into [0, L): x <- x - L floor(x / L).
+ *   pos  3 x n float64 device;  mom  3 x n device, mom_precision 32 or 64.
+ * Drifting changes subtile membership: sort again before the next forces call.
+ */
+p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom, int mom_precision,
+                        double factor);
+
+/*
+ * Vector-Jacobian product of the short-range accelerations with respect to
+ * the positions (derived from Eq. p3m_gravity):
+ *   xbar_k = sum_{j != k, r_kj < x_r} J_kj (abar_k [k active] - abar_j [j active]),
+ *   J_kj = phi(r) I + (phi'(r)/r) x_kj x_kj^T,   phi = -G m B.
+ * Active means receiver of the last p3m_sr_build_pairs.  Every particle gets a
+ * gradient (suppliers move the receivers' accelerations too).
+ *   pos          3 x n float64 SoA device (sorted order)
+ *   acc_bar      3 x n device, float (precision 32) or double (64)
+ *   pos_bar_out  3 x n device, same type; every row is overwritten.
+ */
+p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precision, const void* acc_bar,
+                      void* pos_bar_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* P3M_SR_H */

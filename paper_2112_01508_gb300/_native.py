@@ -1,0 +1,181 @@
+"""ctypes binding of the C ABI in include/p3m_sr.h (argument marshalling only).
+
+Each ``p3m_sr_*`` function here has the name and argument order of the C entry
+point and returns its integer status.  The library must have been built
+(``paper_2112_01508_gb300.buildlib.build()``); loading fails loudly otherwise --
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .buildlib import LIB
+
+P3M_OK = 0
+P3M_ERR_INVALID = 1
+P3M_ERR_TOO_FEW_TILES = 2
+P3M_ERR_OOM = 3
+P3M_ERR_CUDA = 4
+P3M_ERR_TIMEOUT = 5
+P3M_ERR_NONFINITE = 6
+P3M_ERR_STATE = 7
+
+STATUS_NAMES = {
+    0: "P3M_OK", 1: "P3M_ERR_INVALID", 2: "P3M_ERR_TOO_FEW_TILES", 3: "P3M_ERR_OOM", 4: "P3M_ERR_CUDA",
+    5: "P3M_ERR_TIMEOUT", 6: "P3M_ERR_NONFINITE", 7: "P3M_ERR_STATE",
+}
+
+SOFTENING = {"none": 0, "plummer": 1, "bspline": 2}
+
+# Every symbol declared in include/p3m_sr.h.
+EXPORTS = (
+    "p3m_sr_create", "p3m_sr_destroy", "p3m_sr_last_error", "p3m_sr_sync", "p3m_sr_stats", "p3m_sr_sort",
+    "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
+)
+
+
+class P3MParams(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("box", ctypes.c_double),
+        ("x_s", ctypes.c_double),
+        ("x_r", ctypes.c_double),
+        ("G_m", ctypes.c_double),
+        ("softening", ctypes.c_int),
+        ("eps", ctypes.c_double),
+        ("n_sub", ctypes.c_int * 3),
+        ("n_rung", ctypes.c_int),
+    ]
+
+
+class P3MStats(ctypes.Structure):
+    _fields_ = [
+        ("n_tile", ctypes.c_int),
+        ("n_sub", ctypes.c_int * 3),
+        ("n_subtiles", ctypes.c_int64),
+        ("n_active", ctypes.c_int64),
+        ("n_chunks", ctypes.c_int64),
+        ("pairs_last", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+        ("force_kernel_ms", ctypes.c_double),
+        ("vjp_kernel_ms", ctypes.c_double),
+    ]
+
+
+class P3MError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libp3m_sr.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB):
+            raise ImportError(
+                f"{LIB} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB)
+        p, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.p3m_sr_create.argtypes = [ctypes.POINTER(P3MParams), p, ctypes.POINTER(p)]
+        L.p3m_sr_create.restype = i
+        L.p3m_sr_destroy.argtypes = [p]
+        L.p3m_sr_destroy.restype = None
+        L.p3m_sr_last_error.argtypes = [p]
+        L.p3m_sr_last_error.restype = ctypes.c_char_p
+        L.p3m_sr_sync.argtypes = [p]
+        L.p3m_sr_sync.restype = i
+        L.p3m_sr_stats.argtypes = [p, ctypes.POINTER(P3MStats)]
+        L.p3m_sr_stats.restype = i
+        L.p3m_sr_sort.argtypes = [p, p, ctypes.POINTER(p), ctypes.POINTER(i), i, p, p]
+        L.p3m_sr_sort.restype = i
+        L.p3m_sr_build_pairs.argtypes = [p, p, i]
+        L.p3m_sr_build_pairs.restype = i
+        L.p3m_sr_forces.argtypes = [p, p, i, p]
+        L.p3m_sr_forces.restype = i
+        L.p3m_sr_assign_rungs.argtypes = [p, p, i, d, d, d, p]
+        L.p3m_sr_assign_rungs.restype = i
+        L.p3m_sr_kick.argtypes = [p, p, i, p, i, p, i, ctypes.POINTER(d)]
+        L.p3m_sr_kick.restype = i
+        L.p3m_sr_drift.argtypes = [p, p, p, i, d]
+        L.p3m_sr_drift.restype = i
+        L.p3m_sr_vjp.argtypes = [p, p, i, p, p]
+        L.p3m_sr_vjp.restype = i
+        _lib = L
+        return L
+
+
+# ---- thin wrappers with the C names ------------------------------------------
+
+def p3m_sr_create(params: P3MParams, cuda_stream: int):
+    ctx = ctypes.c_void_p()
+    st = load().p3m_sr_create(ctypes.byref(params), ctypes.c_void_p(cuda_stream), ctypes.byref(ctx))
+    return st, ctx
+
+
+def p3m_sr_destroy(ctx) -> None:
+    load().p3m_sr_destroy(ctx)
+
+
+def p3m_sr_last_error(ctx) -> str:
+    return load().p3m_sr_last_error(ctx).decode(errors="replace")
+
+
+def p3m_sr_sync(ctx) -> int:
+    return load().p3m_sr_sync(ctx)
+
+
+def p3m_sr_stats(ctx):
+    out = P3MStats()
+    st = load().p3m_sr_stats(ctx, ctypes.byref(out))
+    return st, out
+
+
+def p3m_sr_sort(ctx, pos_ptr: int, carry_ptrs, carry_bytes, perm_out_ptr, subtile_id_out_ptr) -> int:
+    n = len(carry_ptrs)
+    arr = (ctypes.c_void_p * max(n, 1))(*[ctypes.c_void_p(c) for c in carry_ptrs])
+    nb = (ctypes.c_int * max(n, 1))(*list(carry_bytes))
+    return load().p3m_sr_sort(ctx, ctypes.c_void_p(pos_ptr), arr if n else None, nb if n else None, n,
+                              ctypes.c_void_p(perm_out_ptr or 0), ctypes.c_void_p(subtile_id_out_ptr or 0))
+
+
+def p3m_sr_build_pairs(ctx, rung_ptr, rung_min: int) -> int:
+    return load().p3m_sr_build_pairs(ctx, ctypes.c_void_p(rung_ptr or 0), int(rung_min))
+
+
+def p3m_sr_forces(ctx, pos_ptr: int, precision: int, acc_ptr: int) -> int:
+    return load().p3m_sr_forces(ctx, ctypes.c_void_p(pos_ptr), int(precision), ctypes.c_void_p(acc_ptr))
+
+
+def p3m_sr_assign_rungs(ctx, acc_ptr: int, acc_precision: int, dt: float, eta: float, eps: float, rung_ptr: int) -> int:
+    return load().p3m_sr_assign_rungs(ctx, ctypes.c_void_p(acc_ptr), int(acc_precision), float(dt), float(eta),
+                                      float(eps), ctypes.c_void_p(rung_ptr))
+
+
+def p3m_sr_kick(ctx, mom_ptr, mom_precision, acc_ptr, acc_precision, rung_ptr, rung_min, kick_factor) -> int:
+    kf = (ctypes.c_double * len(kick_factor))(*[float(k) for k in kick_factor])
+    return load().p3m_sr_kick(ctx, ctypes.c_void_p(mom_ptr), int(mom_precision), ctypes.c_void_p(acc_ptr),
+                              int(acc_precision), ctypes.c_void_p(rung_ptr or 0), int(rung_min), kf)
+
+
+def p3m_sr_drift(ctx, pos_ptr, mom_ptr, mom_precision, factor) -> int:
+    return load().p3m_sr_drift(ctx, ctypes.c_void_p(pos_ptr), ctypes.c_void_p(mom_ptr), int(mom_precision),
+                               float(factor))
+
+
+def p3m_sr_vjp(ctx, pos_ptr, precision, acc_bar_ptr, pos_bar_ptr) -> int:
+    return load().p3m_sr_vjp(ctx, ctypes.c_void_p(pos_ptr), int(precision), ctypes.c_void_p(acc_bar_ptr),
+                             ctypes.c_void_p(pos_bar_ptr))

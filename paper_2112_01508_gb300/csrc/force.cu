@@ -1,0 +1,689 @@
+// Receiver work lists, the short-range pair-force kernels (FP32 and FP64) and
+// the adjoint (VJP) kernels.
+//
+// Paper design (Section 2.1.3): tiles of side >= x_r, subtiles inside them,
+// precomputed subtile pairings inside a "blocky ball" of radius x_r, a
+// squared-distance rejection r^2 >= x_r^2 before the force, image shift n'
+// known per subtile pair, particles stored in tile -> subtile -> particle
+// order.  Receivers are the particles on active rungs (Section 2.2.2).
+//
+// GB300 design: the work unit is a receiver chunk -- up to 32 consecutive
+// receivers of one tile, one per warp lane.  A warp owns a chunk and:
+//   1. builds the chunk's frame (origin: the subtile of its first receiver)
+//      and tight bounding box;
+//   2. enumerates, 32 candidates at a time across the lanes, the subtiles of
+//      the blocky ball around the chunk's subtile block (the paper's subtile
+//      pairing generalised to a block of subtiles), keeps those whose box gap
+//      to the chunk's bounding box is below x_r, and appends their particle
+//      ranges to a per-warp list in shared memory;
+//   3. walks the concatenated supplier ranges 32 at a time: each lane loads
+//      one supplier j (FP32 coordinates relative to its subtile origin, moved
+//      into the chunk frame by the integer subtile offset), tests it against
+//      the chunk's bounding box, and the survivors are broadcast to all lanes
+//      with warp shuffles, where every lane evaluates its own (i, j) pair.
+// Chunks are handed out dynamically through an atomic counter (persistent
+// warps), which balances the strongly varying cost of clustered regions.
+#include <algorithm>
+#include <cmath>
+
+#include "ctx.cuh"
+#include "erfcx_fit.h"
+#include "pair_math.cuh"
+
+namespace p3m {
+
+constexpr int kForceThreads = 128;
+constexpr int kForceWarps = kForceThreads / kWarp;
+constexpr int kListCap = 128;  // supplier subtiles buffered per warp
+
+static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// Prologue kernels.
+// ---------------------------------------------------------------------------
+
+// FP32 coordinates relative to the particle's subtile origin, plus the id bits.
+__global__ void k_rel4(const double* __restrict__ pos, const int* __restrict__ cell, int64_t n, Geometry g,
+                       float4* __restrict__ rel4) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int id = cell[i];
+  int gx, gy, gz;
+  decode_subtile(g, id, gx, gy, gz);
+  float rx = (float)__dsub_rn(pos[i], __dmul_rn((double)gx, g.side64[0]));
+  float ry = (float)__dsub_rn(pos[n + i], __dmul_rn((double)gy, g.side64[1]));
+  float rz = (float)__dsub_rn(pos[2 * n + i], __dmul_rn((double)gz, g.side64[2]));
+  rel4[i] = make_float4(rx, ry, rz, __int_as_float(id));
+}
+
+__global__ void k_active_flags(const int8_t* __restrict__ rung, int64_t n, int rung_min, int8_t* __restrict__ flag,
+                               int* __restrict__ act) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  if (i == n) {
+    act[n] = 0;
+    return;
+  }
+  int a = rung ? (rung[i] >= rung_min) : 1;
+  flag[i] = (int8_t)a;
+  act[i] = a;
+}
+
+__global__ void k_compact(const int8_t* __restrict__ flag, const int* __restrict__ act_scan, int64_t n,
+                          int* __restrict__ active_idx) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (flag[i]) active_idx[act_scan[i]] = (int)i;
+}
+
+// Chunks per tile: ceil(receivers in tile / 32).
+__global__ void k_tile_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int64_t n_tiles,
+                              int nsub3, int* __restrict__ tile_chunks) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > n_tiles) return;
+  if (t == n_tiles) {
+    tile_chunks[n_tiles] = 0;
+    return;
+  }
+  int p0 = offsets[t * nsub3], p1 = offsets[(t + 1) * nsub3];
+  int a0 = act_scan ? act_scan[p0] : p0;
+  int a1 = act_scan ? act_scan[p1] : p1;
+  tile_chunks[t] = (a1 - a0 + kChunk - 1) / kChunk;
+}
+
+__global__ void k_write_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int64_t n_tiles,
+                               int nsub3, const int* __restrict__ tile_chunks, Chunk* __restrict__ chunks,
+                               int* __restrict__ n_chunks_out, int* __restrict__ n_active_out, int64_t n) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    *n_chunks_out = tile_chunks[n_tiles];
+    if (n_active_out) *n_active_out = act_scan ? act_scan[n] : (int)n;
+  }
+  if (t >= n_tiles) return;
+  int p0 = offsets[t * nsub3], p1 = offsets[(t + 1) * nsub3];
+  int a0 = act_scan ? act_scan[p0] : p0;
+  int a1 = act_scan ? act_scan[p1] : p1;
+  int c0 = tile_chunks[t];
+  for (int k = 0; a0 + k * kChunk < a1; ++k) {
+    Chunk c;
+    c.start = a0 + k * kChunk;
+    c.count = min(kChunk, a1 - c.start);
+    chunks[c0 + k] = c;
+  }
+}
+
+// Masked abar for the VJP: abar_i * [i active].
+__global__ void k_abar_f32(const float* __restrict__ abar, const int8_t* __restrict__ flag, int all_active,
+                           int64_t n, float4* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float m = (all_active || flag[i]) ? 1.0f : 0.0f;
+  out[i] = make_float4(abar[i] * m, abar[n + i] * m, abar[2 * n + i] * m, 0.0f);
+}
+
+__global__ void k_abar_f64(const double* __restrict__ abar, const int8_t* __restrict__ flag, int all_active,
+                           int64_t n, double* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double m = (all_active || flag[i]) ? 1.0 : 0.0;
+  out[i] = abar[i] * m;
+  out[n + i] = abar[n + i] * m;
+  out[2 * n + i] = abar[2 * n + i] * m;
+}
+
+// ---------------------------------------------------------------------------
+// The traversal kernel.
+// ---------------------------------------------------------------------------
+
+struct TraversalArgs {
+  Geometry g;
+  ForceConsts f;
+  SeriesConsts sc;
+  const double* pos;          // FP64 path positions
+  const float4* rel4;         // FP32 path coordinates
+  const int* offsets;         // S + 1 subtile offsets
+  const int* cell;            // sorted subtile ids
+  const Chunk* chunks;
+  const int* n_chunks;        // device count
+  int* counter;               // dynamic chunk counter (zeroed before launch)
+  const int* active_idx;      // receiver list (nullptr: chunk ranges are particle indices)
+  int64_t n;
+  void* out;                  // acc (forward) or xbar (vjp), 3 x n
+  // vjp only
+  const float4* abar4;        // masked abar FP32
+  const double* abar_d;       // masked abar FP64, 3 x n
+  unsigned long long* pairs;  // interacting ordered pairs
+};
+
+template <class Real>
+struct Vec3 {
+  Real x, y, z;
+};
+
+__device__ __forceinline__ float redux_min_f(float v) {
+  float r;
+  asm("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ float redux_max_f(float v) {
+  float r;
+  asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ double warp_min_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_min(float v) { return redux_min_f(v); }
+__device__ __forceinline__ float warp_max(float v) { return redux_max_f(v); }
+__device__ __forceinline__ double warp_min(double v) { return warp_min_d(v); }
+__device__ __forceinline__ double warp_max(double v) { return warp_max_d(v); }
+
+__device__ __forceinline__ unsigned pack_delta(int dx, int dy, int dz) {
+  return ((unsigned)(dx + 512) << 20) | ((unsigned)(dy + 512) << 10) | (unsigned)(dz + 512);
+}
+__device__ __forceinline__ void unpack_delta(unsigned p, int& dx, int& dy, int& dz) {
+  dx = (int)(p >> 20) - 512;
+  dy = (int)((p >> 10) & 1023u) - 512;
+  dz = (int)(p & 1023u) - 512;
+}
+
+struct WarpList {
+  int start[kListCap];
+  int pre[kListCap];       // exclusive prefix of the supplier counts
+  unsigned delta[kListCap];
+};
+
+template <class Real>
+__device__ __forceinline__ Real sq(Real v) {
+  return v * v;
+}
+
+// Process the suppliers of the list entries [0, nlist) (total suppliers `total`).
+template <class Real, bool VJP, int SOFT>
+__device__ __forceinline__ void process_list(const TraversalArgs& a, const WarpList& L, int nlist, int total, int lane,
+                                             const int g0[3], const Vec3<Real>& pi, const Vec3<Real>& lo,
+                                             const Vec3<Real>& hi, const Vec3<Real>& abar_i, Vec3<Real>& acc,
+                                             int& hits) {
+  const unsigned full = 0xffffffffu;
+  for (int b = 0; b < total; b += kWarp) {
+    int f = b + lane;
+    bool have = f < total;
+    Vec3<Real> pj = {Real(0), Real(0), Real(0)};
+    Vec3<Real> aj = {Real(0), Real(0), Real(0)};
+    bool keep = false;
+    if (have) {
+      // entry e: last entry with pre[e] <= f
+      int lo_e = 0, hi_e = nlist - 1;
+      while (lo_e < hi_e) {
+        int mid = (lo_e + hi_e + 1) >> 1;
+        if (L.pre[mid] <= f) lo_e = mid; else hi_e = mid - 1;
+      }
+      int j = L.start[lo_e] + (f - L.pre[lo_e]);
+      int dx, dy, dz;
+      unpack_delta(L.delta[lo_e], dx, dy, dz);
+      if constexpr (sizeof(Real) == 4) {
+        float4 r = a.rel4[j];
+        pj.x = fmaf((float)dx, a.g.side32[0], r.x);
+        pj.y = fmaf((float)dy, a.g.side32[1], r.y);
+        pj.z = fmaf((float)dz, a.g.side32[2], r.z);
+        if (VJP) {
+          float4 q = a.abar4[j];
+          aj.x = q.x; aj.y = q.y; aj.z = q.z;
+        }
+      } else {
+        // absolute coordinates of the image of j nearest to the chunk
+        int gx = g0[0] + dx, gy = g0[1] + dy, gz = g0[2] + dz;
+        double sx = gx < 0 ? -a.g.box : (gx >= a.g.M[0] ? a.g.box : 0.0);
+        double sy = gy < 0 ? -a.g.box : (gy >= a.g.M[1] ? a.g.box : 0.0);
+        double sz = gz < 0 ? -a.g.box : (gz >= a.g.M[2] ? a.g.box : 0.0);
+        pj.x = a.pos[j] + sx;
+        pj.y = a.pos[a.n + j] + sy;
+        pj.z = a.pos[2 * a.n + j] + sz;
+        if (VJP) {
+          aj.x = a.abar_d[j]; aj.y = a.abar_d[a.n + j]; aj.z = a.abar_d[2 * a.n + j];
+        }
+      }
+      // distance from j to the chunk's bounding box
+      Real tx = fmax(fmax(lo.x - pj.x, pj.x - hi.x), Real(0));
+      Real ty = fmax(fmax(lo.y - pj.y, pj.y - hi.y), Real(0));
+      Real tz = fmax(fmax(lo.z - pj.z, pj.z - hi.z), Real(0));
+      keep = (tx * tx + ty * ty + tz * tz) < Real(a.f.margin2_f);
+    }
+    unsigned m = __ballot_sync(full, keep);
+    while (m) {
+      int src = __ffs(m) - 1;
+      m &= m - 1;
+      Real xj = __shfl_sync(full, pj.x, src);
+      Real yj = __shfl_sync(full, pj.y, src);
+      Real zj = __shfl_sync(full, pj.z, src);
+      Real dx = pi.x - xj, dy = pi.y - yj, dz = pi.z - zj;
+      Real r2 = dx * dx + dy * dy + dz * dz;
+      bool hit;
+      if constexpr (sizeof(Real) == 4) hit = r2 < a.f.xr2_f; else hit = r2 < a.f.xr2_d;
+      Vec3<Real> vj;
+      if (VJP) {
+        vj.x = __shfl_sync(full, aj.x, src);
+        vj.y = __shfl_sync(full, aj.y, src);
+        vj.z = __shfl_sync(full, aj.z, src);
+      }
+      if (__any_sync(full, hit)) {
+        Real B, D = Real(0);
+        if constexpr (sizeof(Real) == 4) {
+          float Dm = 0.f;
+          B = bracket_main_f32<SOFT, VJP>(r2, a.f, Dm);
+          D = Dm;
+          // forward: a zero displacement contributes nothing, so r = 0 skips the
+          // softened branch; the VJP needs B(0) for coincident distinct particles
+          bool rare = hit && (r2 < a.f.rsw2_f) && (VJP || r2 > 0.0f);
+          if (__any_sync(full, rare)) {
+            float Ds = 0.f;
+            float Bs = bracket_soft_f32<SOFT, VJP>(r2, a.f, a.sc, Ds);
+            if (rare) { B = Bs; D = Ds; }
+          }
+        } else {
+          B = (hit && (VJP || r2 > 0.0)) ? bracket_f64<SOFT, VJP>(r2, a.f, a.sc, D) : 0.0;
+        }
+        if (!hit || (!VJP && r2 == Real(0))) { B = Real(0); D = Real(0); }
+        if (VJP) {
+          Real vx = abar_i.x - vj.x, vy = abar_i.y - vj.y, vz = abar_i.z - vj.z;
+          Real c = D * (dx * vx + dy * vy + dz * vz);
+          acc.x += B * vx + c * dx;
+          acc.y += B * vy + c * dy;
+          acc.z += B * vz + c * dz;
+        } else {
+          acc.x += B * dx;
+          acc.y += B * dy;
+          acc.z += B * dz;
+        }
+        hits += hit ? 1 : 0;
+      }
+    }
+  }
+}
+
+template <class Real, bool VJP, int SOFT>
+__global__ void __launch_bounds__(kForceThreads) k_traverse(TraversalArgs a) {
+  __shared__ WarpList lists[kForceWarps];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  WarpList& L = lists[threadIdx.x >> 5];
+  const Geometry& g = a.g;
+  const int n_chunks = *a.n_chunks;
+  unsigned long long pair_total = 0;
+
+  for (;;) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(a.counter, 1);
+    c = __shfl_sync(full, c, 0);
+    if (c >= n_chunks) break;
+    const Chunk ch = a.chunks[c];
+    const bool valid = lane < ch.count;
+    int pidx = 0;
+    if (valid) pidx = a.active_idx ? a.active_idx[ch.start + lane] : ch.start + lane;
+
+    // receiver position, its subtile and the chunk frame
+    int gi[3] = {0, 0, 0};
+    Vec3<Real> pi;
+    float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
+    {
+      int id = 0;
+      if constexpr (sizeof(Real) == 4) {
+        if (valid) ri = a.rel4[pidx];
+        id = __float_as_int(ri.w);
+      } else {
+        if (valid) id = a.cell[pidx];
+      }
+      if (valid) decode_subtile(g, id, gi[0], gi[1], gi[2]);
+    }
+    int g0[3];
+    g0[0] = __shfl_sync(full, gi[0], 0);
+    g0[1] = __shfl_sync(full, gi[1], 0);
+    g0[2] = __shfl_sync(full, gi[2], 0);
+    const int e[3] = {gi[0] - g0[0], gi[1] - g0[1], gi[2] - g0[2]};
+    if constexpr (sizeof(Real) == 4) {
+      pi.x = fmaf((float)e[0], g.side32[0], ri.x);
+      pi.y = fmaf((float)e[1], g.side32[1], ri.y);
+      pi.z = fmaf((float)e[2], g.side32[2], ri.z);
+    } else {
+      pi.x = a.pos[pidx];
+      pi.y = a.pos[a.n + pidx];
+      pi.z = a.pos[2 * a.n + pidx];
+    }
+    const Real big = Real(1e30);
+    Vec3<Real> lo, hi;
+    lo.x = warp_min(valid ? pi.x : big);
+    lo.y = warp_min(valid ? pi.y : big);
+    lo.z = warp_min(valid ? pi.z : big);
+    hi.x = warp_max(valid ? pi.x : -big);
+    hi.y = warp_max(valid ? pi.y : -big);
+    hi.z = warp_max(valid ? pi.z : -big);
+    if (!valid) { pi.x = big; pi.y = big; pi.z = big; }
+    Vec3<Real> abar_i = {Real(0), Real(0), Real(0)};
+    if (VJP && valid) {
+      if constexpr (sizeof(Real) == 4) {
+        float4 q = a.abar4[pidx];
+        abar_i.x = q.x; abar_i.y = q.y; abar_i.z = q.z;
+      } else {
+        abar_i.x = a.abar_d[pidx]; abar_i.y = a.abar_d[a.n + pidx]; abar_i.z = a.abar_d[2 * a.n + pidx];
+      }
+    }
+    int elo[3], ehi[3], ext[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      elo[d] = __reduce_min_sync(full, valid ? e[d] : 1 << 20) - g.R[d];
+      ehi[d] = __reduce_max_sync(full, valid ? e[d] : -(1 << 20)) + g.R[d];
+      ext[d] = ehi[d] - elo[d] + 1;
+    }
+    // frame origin of the subtile block (chunk frame for FP32, absolute for FP64)
+    Real org[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if constexpr (sizeof(Real) == 4) org[d] = 0.0f;
+      else org[d] = (double)g0[d] * g.side64[d];
+    }
+    const int ncand = ext[0] * ext[1] * ext[2];
+    Vec3<Real> acc = {Real(0), Real(0), Real(0)};
+    int hits = 0;
+    int nlist = 0, total = 0;
+    for (int cb = 0; cb < ncand; cb += kWarp) {
+      int cc = cb + lane;
+      bool take = false;
+      int start = 0, cnt = 0;
+      unsigned dpk = 0;
+      if (cc < ncand) {
+        int dz = cc % ext[2];
+        int t = cc / ext[2];
+        int dy = t % ext[1];
+        int dx = t / ext[1];
+        dx += elo[0]; dy += elo[1]; dz += elo[2];
+        Real side[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if constexpr (sizeof(Real) == 4) side[d] = g.side32[d]; else side[d] = g.side64[d];
+        }
+        const int dd[3] = {dx, dy, dz};
+        const Real blo[3] = {lo.x, lo.y, lo.z}, bhi[3] = {hi.x, hi.y, hi.z};
+        Real gap2 = Real(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          Real jlo = org[d] + Real(dd[d]) * side[d];
+          Real jhi = jlo + side[d];
+          Real gp = fmax(fmax(blo[d] - jhi, jlo - bhi[d]), Real(0));
+          gap2 += gp * gp;
+        }
+        if (gap2 < Real(a.f.margin2_f)) {
+          int gx = g0[0] + dx, gy = g0[1] + dy, gz = g0[2] + dz;
+          gx += gx < 0 ? g.M[0] : (gx >= g.M[0] ? -g.M[0] : 0);
+          gy += gy < 0 ? g.M[1] : (gy >= g.M[1] ? -g.M[1] : 0);
+          gz += gz < 0 ? g.M[2] : (gz >= g.M[2] ? -g.M[2] : 0);
+          int sid = encode_subtile(g, gx, gy, gz);
+          start = a.offsets[sid];
+          cnt = a.offsets[sid + 1] - start;
+          take = cnt > 0;
+          dpk = pack_delta(dx, dy, dz);
+        }
+      }
+      unsigned tm = __ballot_sync(full, take);
+      int ntake = __popc(tm);
+      if (ntake == 0) continue;
+      if (nlist + ntake > kListCap) {
+        __syncwarp();
+        process_list<Real, VJP, SOFT>(a, L, nlist, total, lane, g0, pi, lo, hi, abar_i, acc, hits);
+        __syncwarp();
+        nlist = 0;
+        total = 0;
+      }
+      // inclusive scan of the counts of the taken lanes
+      int v = take ? cnt : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(full, v, o);
+        if (lane >= o) v += u;
+      }
+      int round_total = __shfl_sync(full, v, 31);
+      if (take) {
+        int slot = nlist + __popc(tm & ((1u << lane) - 1u));
+        L.start[slot] = start;
+        L.pre[slot] = total + v - cnt;
+        L.delta[slot] = dpk;
+      }
+      nlist += ntake;
+      total += round_total;
+    }
+    __syncwarp();
+    if (nlist > 0) process_list<Real, VJP, SOFT>(a, L, nlist, total, lane, g0, pi, lo, hi, abar_i, acc, hits);
+    __syncwarp();
+
+    if (valid) {
+      const Real s = -Real(a.f.G_m);
+      if constexpr (sizeof(Real) == 4) {
+        float* o = (float*)a.out;
+        o[pidx] = s * acc.x;
+        o[a.n + pidx] = s * acc.y;
+        o[2 * a.n + pidx] = s * acc.z;
+      } else {
+        double* o = (double*)a.out;
+        o[pidx] = s * acc.x;
+        o[a.n + pidx] = s * acc.y;
+        o[2 * a.n + pidx] = s * acc.z;
+      }
+      hits -= 1;  // the receiver met itself once (r = 0)
+    }
+    pair_total += (unsigned long long)__reduce_add_sync(full, (unsigned)hits);
+  }
+  if (lane == 0 && pair_total) atomicAdd(a.pairs, pair_total);
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+
+static SeriesConsts make_series() {
+  SeriesConsts s{};
+  const double two_over_sqrt_pi = 1.12837916709551257390;
+  // h(u) = sum_m H_m u^{2m},  H_m = (2/sqrt(pi)) (-1)^m 2(m+1) / ((m+1)! (2m+3))
+  double H[kHTermsD + 1];
+  double fact = 1.0;
+  for (int m = 0; m <= kHTermsD; ++m) {
+    fact *= (double)(m + 1);
+    H[m] = two_over_sqrt_pi * ((m & 1) ? -1.0 : 1.0) * 2.0 * (m + 1) / (fact * (2.0 * m + 3.0));
+  }
+  for (int m = 0; m < kHTermsD; ++m) {
+    s.h_d[m] = H[m];
+    s.hd_d[m] = 2.0 * (m + 1) * H[m + 1];  // h'(u)/u
+  }
+  for (int m = 0; m < kHTermsF; ++m) {
+    s.h_f[m] = (float)s.h_d[m];
+    s.hd_f[m] = (float)s.hd_d[m];
+  }
+  return s;
+}
+
+template <class Real, bool VJP, int SOFT>
+static cudaError_t launch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
+  static int blocks_per_sm = 0;
+  if (blocks_per_sm == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_traverse<Real, VJP, SOFT>, kForceThreads, 0);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  unsigned grid = (unsigned)(ctx->num_sms * blocks_per_sm);
+  const int slot = VJP ? 1 : 0;
+  cudaEventRecord(ctx->kt_ev[2 * slot], ctx->stream);
+  k_traverse<Real, VJP, SOFT><<<grid, kForceThreads, 0, ctx->stream>>>(a);
+  ++ctx->launches;
+  cudaEventRecord(ctx->kt_ev[2 * slot + 1], ctx->stream);
+  ctx->kt_pending[slot] = true;
+  return cudaGetLastError();
+}
+
+template <class Real, bool VJP>
+static cudaError_t dispatch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
+  switch (ctx->prm.softening) {
+    case P3M_SOFT_NONE: return launch_traverse<Real, VJP, P3M_SOFT_NONE>(ctx, a);
+    case P3M_SOFT_PLUMMER: return launch_traverse<Real, VJP, P3M_SOFT_PLUMMER>(ctx, a);
+    default: return launch_traverse<Real, VJP, P3M_SOFT_BSPLINE>(ctx, a);
+  }
+}
+
+static p3m_status build_chunks(p3m_sr_ctx* ctx, const int* act_scan, Chunk* chunks, int* n_chunks_dev,
+                               int* n_active_dev) {
+  cudaStream_t s = ctx->stream;
+  const int64_t nt = ctx->n_tiles;
+  k_tile_chunks<<<blocks_for(nt + 1, 256), 256, 0, s>>>(ctx->offsets, act_scan, nt, ctx->geo.nsub3,
+                                                         ctx->tile_chunks);
+  ++ctx->launches;
+  p3m_status st = cuda_check(ctx, cudaGetLastError(), "tile chunk kernel");
+  if (st != P3M_OK) return st;
+  st = cuda_check(ctx, scan_exclusive_i32(ctx->tile_chunks, ctx->tile_chunks, nt + 1, ctx->scan_scratch, s, &ctx->launches),
+                  "chunk scan");
+  if (st != P3M_OK) return st;
+  k_write_chunks<<<blocks_for(nt > 0 ? nt : 1, 256), 256, 0, s>>>(ctx->offsets, act_scan, nt, ctx->geo.nsub3,
+                                                                   ctx->tile_chunks, chunks, n_chunks_dev,
+                                                                   n_active_dev, ctx->n);
+  ++ctx->launches;
+  return cuda_check(ctx, cudaGetLastError(), "write chunks kernel");
+}
+
+p3m_status ensure_all_chunks(p3m_sr_ctx* ctx) {
+  if (ctx->all_chunks_built) return P3M_OK;
+  p3m_status st = build_chunks(ctx, nullptr, ctx->chunks_all, ctx->dev_small + 1, nullptr);
+  if (st == P3M_OK) ctx->all_chunks_built = true;
+  return st;
+}
+
+static TraversalArgs base_args(p3m_sr_ctx* ctx) {
+  static SeriesConsts series = make_series();
+  TraversalArgs a{};
+  a.g = ctx->geo;
+  a.f = ctx->fc;
+  a.sc = series;
+  a.offsets = ctx->offsets;
+  a.cell = ctx->cell;
+  a.n = ctx->n;
+  a.rel4 = ctx->rel4;
+  a.pairs = ctx->pair_count;
+  return a;
+}
+
+static p3m_status prepare_rel4(p3m_sr_ctx* ctx, const double* pos) {
+  if (ctx->n == 0) return P3M_OK;
+  k_rel4<<<blocks_for(ctx->n, 256), 256, 0, ctx->stream>>>(pos, ctx->cell, ctx->n, ctx->geo, ctx->rel4);
+  ++ctx->launches;
+  return cuda_check(ctx, cudaGetLastError(), "rel4 kernel");
+}
+
+}  // namespace p3m
+
+using namespace p3m;
+
+extern "C" p3m_status p3m_sr_build_pairs(p3m_sr_ctx* ctx, const int8_t* rung, int rung_min) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (!ctx->sorted) return fail(ctx, P3M_ERR_STATE, "build_pairs: call p3m_sr_sort first");
+  p3m_status st = poll_latched(ctx);
+  if (st != P3M_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  ctx->all_active = (rung == nullptr);
+  const int* act_scan = nullptr;
+  if (!ctx->all_active) {
+    k_active_flags<<<blocks_for(n + 1, 256), 256, 0, s>>>(rung, n, rung_min, ctx->active_flag, ctx->act_scan);
+  ++ctx->launches;
+    if ((st = cuda_check(ctx, cudaGetLastError(), "active flags")) != P3M_OK) return st;
+    st = cuda_check(ctx, scan_exclusive_i32(ctx->act_scan, ctx->act_scan, n + 1, ctx->scan_scratch, s, &ctx->launches), "scan");
+    if (st != P3M_OK) return st;
+    if (n > 0) {
+      k_compact<<<blocks_for(n, 256), 256, 0, s>>>(ctx->active_flag, ctx->act_scan, n, ctx->active_idx);
+  ++ctx->launches;
+      if ((st = cuda_check(ctx, cudaGetLastError(), "compact")) != P3M_OK) return st;
+    }
+    act_scan = ctx->act_scan;
+  }
+  st = build_chunks(ctx, act_scan, ctx->chunks, ctx->dev_small + 0, ctx->dev_small + 2);
+  if (st != P3M_OK) return st;
+  ctx->pairs_built = true;
+  return P3M_OK;
+}
+
+extern "C" p3m_status p3m_sr_forces(p3m_sr_ctx* ctx, const double* pos, int precision, void* acc_out) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (precision != 32 && precision != 64) return fail(ctx, P3M_ERR_INVALID, "forces: precision must be 32 or 64");
+  if (ctx->n > 0 && (!pos || !acc_out)) return fail(ctx, P3M_ERR_INVALID, "forces: null pointer");
+  if (!ctx->sorted || !ctx->pairs_built)
+    return fail(ctx, P3M_ERR_STATE, "forces: call p3m_sr_sort and p3m_sr_build_pairs first");
+  if (precision == 32 && ctx->prm.x_r > 2.0 * P3M_ERFCX_UMAX * ctx->prm.x_s)
+    return fail(ctx, P3M_ERR_INVALID, "forces: the FP32 path needs x_r <= 4.6 x_s");
+  p3m_status st = poll_latched(ctx);
+  if (st != P3M_OK) return st;
+  cudaStream_t s = ctx->stream;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->pair_count, 0, sizeof(unsigned long long), s), "memset")) != P3M_OK)
+    return st;
+  if (ctx->n == 0) return P3M_OK;
+  if (precision == 32 && (st = prepare_rel4(ctx, pos)) != P3M_OK) return st;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dev_small + 3, 0, sizeof(int), s), "memset")) != P3M_OK) return st;
+  TraversalArgs a = base_args(ctx);
+  a.pos = pos;
+  a.chunks = ctx->chunks;
+  a.n_chunks = ctx->dev_small + 0;
+  a.counter = ctx->dev_small + 3;
+  a.active_idx = ctx->all_active ? nullptr : ctx->active_idx;
+  a.out = acc_out;
+  cudaError_t e = (precision == 32) ? dispatch_traverse<float, false>(ctx, a) : dispatch_traverse<double, false>(ctx, a);
+  if ((st = cuda_check(ctx, e, "force kernel")) != P3M_OK) return st;
+  report_latched(ctx);
+  return P3M_OK;
+}
+
+extern "C" p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precision, const void* acc_bar,
+                                 void* pos_bar_out) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (precision != 32 && precision != 64) return fail(ctx, P3M_ERR_INVALID, "vjp: precision must be 32 or 64");
+  if (ctx->n > 0 && (!pos || !acc_bar || !pos_bar_out)) return fail(ctx, P3M_ERR_INVALID, "vjp: null pointer");
+  if (!ctx->sorted || !ctx->pairs_built)
+    return fail(ctx, P3M_ERR_STATE, "vjp: call p3m_sr_sort and p3m_sr_build_pairs first");
+  if (precision == 32 && ctx->prm.x_r > 2.0 * P3M_ERFCX_UMAX * ctx->prm.x_s)
+    return fail(ctx, P3M_ERR_INVALID, "vjp: the FP32 path needs x_r <= 4.6 x_s");
+  p3m_status st = poll_latched(ctx);
+  if (st != P3M_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->pair_count, 0, sizeof(unsigned long long), s), "memset")) != P3M_OK)
+    return st;
+  if (n == 0) return P3M_OK;
+  if (precision == 32 && !ctx->abar4) {
+    if ((st = cuda_check(ctx, cudaMalloc((void**)&ctx->abar4, sizeof(float4) * n), "cudaMalloc(abar4)")) != P3M_OK)
+      return st;
+  }
+  if (precision == 64 && !ctx->abar_d) {
+    if ((st = cuda_check(ctx, cudaMalloc((void**)&ctx->abar_d, sizeof(double) * 3 * n), "cudaMalloc(abar_d)")) != P3M_OK)
+      return st;
+  }
+  if ((st = ensure_all_chunks(ctx)) != P3M_OK) return st;
+  if (precision == 32 && (st = prepare_rel4(ctx, pos)) != P3M_OK) return st;
+  if (precision == 32)
+    k_abar_f32<<<blocks_for(n, 256), 256, 0, s>>>((const float*)acc_bar, ctx->active_flag, ctx->all_active, n,
+                                                   ctx->abar4);
+  else
+    k_abar_f64<<<blocks_for(n, 256), 256, 0, s>>>((const double*)acc_bar, ctx->active_flag, ctx->all_active, n,
+                                                   ctx->abar_d);
+  ++ctx->launches;
+  if ((st = cuda_check(ctx, cudaGetLastError(), "abar kernel")) != P3M_OK) return st;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dev_small + 4, 0, sizeof(int), s), "memset")) != P3M_OK) return st;
+  TraversalArgs a = base_args(ctx);
+  a.pos = pos;
+  a.chunks = ctx->chunks_all;
+  a.n_chunks = ctx->dev_small + 1;
+  a.counter = ctx->dev_small + 4;
+  a.active_idx = nullptr;
+  a.out = pos_bar_out;
+  a.abar4 = ctx->abar4;
+  a.abar_d = ctx->abar_d;
+  cudaError_t e = (precision == 32) ? dispatch_traverse<float, true>(ctx, a) : dispatch_traverse<double, true>(ctx, a);
+  if ((st = cuda_check(ctx, e, "vjp kernel")) != P3M_OK) return st;
+  report_latched(ctx);
+  return P3M_OK;
+}

@@ -1,0 +1,388 @@
+// Context creation, parameter validation, error latch and the shared int32 scan.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ctx.cuh"
+#include "erfcx_fit.h"
+
+namespace p3m {
+
+p3m_status fail(p3m_sr_ctx* ctx, p3m_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+p3m_status cuda_check(p3m_sr_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return P3M_OK;
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(ctx, P3M_ERR_OOM, m);
+  return fail(ctx, P3M_ERR_CUDA, m);
+}
+
+static p3m_status status_from_bits(p3m_sr_ctx* ctx, int bits) {
+  if (bits & kErrPosition)
+    return fail(ctx, P3M_ERR_NONFINITE, "a position was non-finite or outside [0, L) when binned");
+  if (bits & kErrNonfiniteAcc)
+    return fail(ctx, P3M_ERR_NONFINITE, "a non-finite acceleration was met by the rung assignment");
+  return P3M_OK;
+}
+
+p3m_status poll_latched(p3m_sr_ctx* ctx) {
+  if (ctx->err_event_pending && cudaEventQuery(ctx->err_event) == cudaSuccess) {
+    ctx->err_event_pending = false;
+  }
+  if (!ctx->err_event_pending && *ctx->err_host) return status_from_bits(ctx, *ctx->err_host);
+  return P3M_OK;
+}
+
+void report_latched(p3m_sr_ctx* ctx) {
+  if (ctx->err_event_pending) return;  // the previous report is still in flight
+  cudaMemcpyAsync(ctx->err_host, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaEventRecord(ctx->err_event, ctx->stream);
+  ctx->err_event_pending = true;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int32 (tiles of 4096 per block, recursive over tile sums).
+// ---------------------------------------------------------------------------
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int smem_pad(int i) { return i + (i >> 5); }
+
+__global__ void k_scan_reduce(const int* __restrict__ in, int64_t n, int* __restrict__ sums) {
+  __shared__ int warp_sums[kScanThreads / kWarp];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = threadIdx.x < kScanThreads / kWarp ? warp_sums[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) sums[blockIdx.x] = v;
+  }
+}
+
+__global__ void k_scan_tile(const int* in, int* out, int64_t n, const int* __restrict__ offs) {
+  __shared__ int tile[kScanTile + kScanTile / 32];
+  __shared__ int warp_tot[kScanThreads / kWarp];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int k = 0; k < kScanItems; ++k) {
+    int li = k * kScanThreads + threadIdx.x;
+    int64_t i = base + li;
+    tile[smem_pad(li)] = i < n ? in[i] : 0;
+  }
+  __syncthreads();
+  int vals[kScanItems];
+  int tot = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    vals[k] = tile[smem_pad(threadIdx.x * kScanItems + k)];
+    tot += vals[k];
+  }
+  // exclusive scan of per-thread totals across the block
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = tot;
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  int wpre = 0;
+  for (int w = 0; w < warp; ++w) wpre += warp_tot[w];
+  int run = wpre + inc - tot + (offs ? offs[blockIdx.x] : 0);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    tile[smem_pad(threadIdx.x * kScanItems + k)] = run;
+    run += vals[k];
+  }
+  __syncthreads();
+  for (int k = 0; k < kScanItems; ++k) {
+    int li = k * kScanThreads + threadIdx.x;
+    int64_t i = base + li;
+    if (i < n) out[i] = tile[smem_pad(li)];
+  }
+}
+
+int64_t scan_scratch_ints(int64_t n) {
+  int64_t total = 0;
+  int64_t m = n;
+  while (m > kScanTile) {
+    m = (m + kScanTile - 1) / kScanTile;
+    total += m;
+  }
+  return total + 1;
+}
+
+cudaError_t scan_exclusive_i32(const int* in, int* out, int64_t n, int* scratch, cudaStream_t s, int64_t* launches) {
+  if (n <= 0) return cudaSuccess;
+  int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb == 1) {
+    k_scan_tile<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    ++*launches;
+    return cudaGetLastError();
+  }
+  int* sums = scratch;
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+  ++*launches;
+  cudaError_t e = scan_exclusive_i32(sums, sums, nb, scratch + nb, s, launches);
+  if (e != cudaSuccess) return e;
+  k_scan_tile<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace p3m
+
+using namespace p3m;
+
+// ---------------------------------------------------------------------------
+// Parameter validation and constants.
+// ---------------------------------------------------------------------------
+
+static p3m_status validate(p3m_sr_ctx* ctx, const p3m_sr_params& p) {
+  if (p.n < 0 || p.n > 0x7fffffffLL - 64) return fail(ctx, P3M_ERR_INVALID, "n must be in [0, 2^31 - 64)");
+  if (!(p.box > 0.0) || !std::isfinite(p.box)) return fail(ctx, P3M_ERR_INVALID, "box must be positive");
+  if (!(p.x_s > 0.0) || !std::isfinite(p.x_s)) return fail(ctx, P3M_ERR_INVALID, "x_s must be positive");
+  if (!(p.x_r > 0.0) || !std::isfinite(p.x_r)) return fail(ctx, P3M_ERR_INVALID, "x_r must be positive");
+  if (!std::isfinite(p.G_m)) return fail(ctx, P3M_ERR_INVALID, "G_m must be finite");
+  if (p.softening < 0 || p.softening > 2) return fail(ctx, P3M_ERR_INVALID, "softening must be 0, 1 or 2");
+  if (p.softening != 0 && !(p.eps > 0.0)) return fail(ctx, P3M_ERR_INVALID, "eps must be positive when softened");
+  for (int d = 0; d < 3; ++d)
+    if (p.n_sub[d] < 1 || p.n_sub[d] > 16) return fail(ctx, P3M_ERR_INVALID, "n_sub must be in 1..16");
+  if (p.n_rung < 1 || p.n_rung > 8) return fail(ctx, P3M_ERR_INVALID, "n_rung must be in 1..8");
+  double nt = std::floor(p.box / p.x_r);
+  if (nt < 4.0) return fail(ctx, P3M_ERR_TOO_FEW_TILES, "need at least 4 tiles per dimension (x_r <= L/4)");
+  double r_sw = (p.softening == 0) ? 0.0 : 2.8 * p.eps;
+  if (r_sw / (2.0 * p.x_s) > 1.0)
+    return fail(ctx, P3M_ERR_INVALID, "softening length too large for the split scale (2.8 eps > 2 x_s)");
+  if (r_sw > p.x_r) return fail(ctx, P3M_ERR_INVALID, "softening length exceeds the cutoff");
+  return P3M_OK;
+}
+
+static void setup_geometry(p3m_sr_ctx* ctx) {
+  const p3m_sr_params& p = ctx->prm;
+  Geometry& g = ctx->geo;
+  g.n_t = (int)std::floor(p.box / p.x_r);
+  g.nsub3 = 1;
+  g.S = 1;
+  g.box = p.box;
+  for (int d = 0; d < 3; ++d) {
+    g.ns[d] = p.n_sub[d];
+    g.M[d] = g.n_t * g.ns[d];
+    g.nsub3 *= g.ns[d];
+    g.S *= g.M[d];
+    g.scale64[d] = (double)g.M[d] / p.box;
+    g.side64[d] = p.box / (double)g.M[d];
+    g.side32[d] = (float)g.side64[d];
+    g.R[d] = (int)std::ceil(p.x_r / g.side64[d] * (1.0 + 1e-12));
+  }
+  ctx->n_tiles = (int64_t)g.n_t * g.n_t * g.n_t;
+}
+
+static void setup_force_consts(p3m_sr_ctx* ctx) {
+  const p3m_sr_params& p = ctx->prm;
+  ForceConsts& f = ctx->fc;
+  const double pi = 3.14159265358979323846;
+  const double log2e = 1.44269504088896340736;
+  f.softening = p.softening;
+  f.x_s = p.x_s;
+  f.x_r = p.x_r;
+  f.G_m = p.G_m;
+  f.eps = p.eps;
+  f.eps_b = 2.8 * p.eps;
+  f.r_sw = (p.softening == 0) ? 0.0 : 2.8 * p.eps;
+  f.xr2_f = (float)(p.x_r * p.x_r);
+  f.rsw2_f = (p.softening == 0) ? 1e-37f : (float)(f.r_sw * f.r_sw);
+  f.ce_f = (float)(-log2e / (4.0 * p.x_s * p.x_s));
+  f.kc_f = (float)(P3M_ERFCX_K / (2.0 * p.x_s));
+  f.k2_f = (float)(1.0 / (std::sqrt(pi) * p.x_s));
+  f.k3_f = (float)(1.0 / (2.0 * std::sqrt(pi) * p.x_s * p.x_s * p.x_s));
+  const double c[6] = {P3M_ERFCX_C0, P3M_ERFCX_C1, P3M_ERFCX_C2, P3M_ERFCX_C3, P3M_ERFCX_C4, P3M_ERFCX_C5};
+  for (int k = 0; k < 6; ++k) f.c_f[k] = (float)c[k];
+  f.inv2xs_f = (float)(1.0 / (2.0 * p.x_s));
+  f.hscale_f = (float)(1.0 / (8.0 * p.x_s * p.x_s * p.x_s));
+  f.epsb_f = (float)f.eps_b;
+  f.inv_epsb_f = f.eps_b > 0 ? (float)(1.0 / f.eps_b) : 0.f;
+  f.bnorm_f = f.eps_b > 0 ? (float)(32.0 / (f.eps_b * f.eps_b * f.eps_b)) : 0.f;
+  f.eps2_f = (float)(p.eps * p.eps);
+  f.margin2_f = (float)(p.x_r * p.x_r * (1.0 + 1e-4));
+  f.xr2_d = p.x_r * p.x_r;
+  f.rsw2_d = (p.softening == 0) ? 0.0 : f.r_sw * f.r_sw;
+}
+
+template <class T>
+static p3m_status alloc(p3m_sr_ctx* ctx, T** ptr, int64_t count, const char* what) {
+  size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(ctx, e == cudaErrorMemoryAllocation ? P3M_ERR_OOM : P3M_ERR_CUDA,
+                std::string("cudaMalloc(") + what + ") failed: " + cudaGetErrorString(e));
+  }
+  return P3M_OK;
+}
+
+extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stream, p3m_sr_ctx** out) {
+  if (!out) return P3M_ERR_INVALID;
+  *out = nullptr;
+  if (!params) return P3M_ERR_INVALID;
+  p3m_sr_ctx* ctx = new (std::nothrow) p3m_sr_ctx();
+  if (!ctx) return P3M_ERR_OOM;
+  p3m_status st = validate(ctx, *params);
+  if (st != P3M_OK) {
+    delete ctx;
+    return st;
+  }
+  ctx->prm = *params;
+  ctx->n = params->n;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  setup_geometry(ctx);
+  setup_force_consts(ctx);
+  if (ctx->geo.S > 0x7fffffffLL - 2) {
+    delete ctx;
+    return P3M_ERR_INVALID;
+  }
+  cudaGetDevice(&ctx->device);
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+
+  const int64_t n = ctx->n;
+  const int64_t S = ctx->geo.S;
+  // radix passes over ceil(log2(S)) key bits, at most 8 bits each
+  int key_bits = 1;
+  while (key_bits < 31 && ((int64_t)1 << key_bits) < S) ++key_bits;
+  ctx->radix_passes = (key_bits + 7) / 8;
+  for (int k = 0, left = key_bits; k < ctx->radix_passes; ++k) {
+    int b = (left + (ctx->radix_passes - k) - 1) / (ctx->radix_passes - k);
+    ctx->radix_bits[k] = b;
+    left -= b;
+  }
+  int64_t radix_blocks = (n + 4095) / 4096;
+  ctx->hist_ints = 256 * (radix_blocks > 0 ? radix_blocks : 1);
+  int64_t scan_n = std::max<int64_t>(std::max<int64_t>(S + 1, n + 1), std::max<int64_t>(ctx->hist_ints, ctx->n_tiles + 1));
+  ctx->scan_scratch_ints = scan_scratch_ints(scan_n);
+  ctx->max_chunks = std::min<int64_t>(n, ctx->n_tiles) + (n + kChunk - 1) / kChunk + 1;
+
+#define P3M_ALLOC(ptr, count) \
+  if ((st = alloc(ctx, &(ptr), (count), #ptr)) != P3M_OK) goto fail_alloc;
+  P3M_ALLOC(ctx->keys[0], n);
+  P3M_ALLOC(ctx->keys[1], n);
+  P3M_ALLOC(ctx->vals[0], n);
+  P3M_ALLOC(ctx->vals[1], n);
+  P3M_ALLOC(ctx->offsets, S + 1);
+  P3M_ALLOC(ctx->hist, ctx->hist_ints);
+  P3M_ALLOC(ctx->scan_scratch, ctx->scan_scratch_ints);
+  {
+    char* gt = nullptr;
+    P3M_ALLOC(gt, 32 * n);
+    ctx->gather_tmp = gt;
+  }
+  P3M_ALLOC(ctx->active_flag, n);
+  P3M_ALLOC(ctx->act_scan, n + 1);
+  P3M_ALLOC(ctx->active_idx, n);
+  P3M_ALLOC(ctx->tile_chunks, ctx->n_tiles + 1);
+  P3M_ALLOC(ctx->chunks, ctx->max_chunks);
+  P3M_ALLOC(ctx->chunks_all, ctx->max_chunks);
+  P3M_ALLOC(ctx->dev_small, 16);
+  P3M_ALLOC(ctx->pair_count, 2);
+  P3M_ALLOC(ctx->rel4, n);
+  P3M_ALLOC(ctx->err_dev, 1);
+#undef P3M_ALLOC
+  if (cudaMallocHost((void**)&ctx->err_host, sizeof(int)) != cudaSuccess) {
+    st = fail(ctx, P3M_ERR_OOM, "cudaMallocHost failed");
+    goto fail_alloc;
+  }
+  *ctx->err_host = 0;
+  if (cudaEventCreateWithFlags(&ctx->err_event, cudaEventDisableTiming) != cudaSuccess) {
+    st = fail(ctx, P3M_ERR_CUDA, "cudaEventCreate failed");
+    goto fail_alloc;
+  }
+  for (int k = 0; k < 4; ++k)
+    if (cudaEventCreate(&ctx->kt_ev[k]) != cudaSuccess) {
+      st = fail(ctx, P3M_ERR_CUDA, "cudaEventCreate failed");
+      goto fail_alloc;
+    }
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), ctx->stream), "memset")) != P3M_OK)
+    goto fail_alloc;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dev_small, 0, 16 * sizeof(int), ctx->stream), "memset")) != P3M_OK)
+    goto fail_alloc;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->pair_count, 0, 2 * sizeof(unsigned long long), ctx->stream),
+                       "memset")) != P3M_OK)
+    goto fail_alloc;
+  *out = ctx;
+  return P3M_OK;
+fail_alloc:
+  p3m_sr_destroy(ctx);
+  return st;
+}
+
+extern "C" void p3m_sr_destroy(p3m_sr_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  void* ptrs[] = {ctx->keys[0], ctx->keys[1], ctx->vals[0], ctx->vals[1], ctx->offsets, ctx->hist,
+                  ctx->scan_scratch, ctx->gather_tmp, ctx->active_flag, ctx->act_scan, ctx->active_idx,
+                  ctx->tile_chunks, ctx->chunks, ctx->chunks_all, ctx->dev_small, ctx->pair_count,
+                  ctx->rel4, ctx->abar4, ctx->abar_d, ctx->err_dev};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (ctx->err_host) cudaFreeHost(ctx->err_host);
+  if (ctx->err_event) cudaEventDestroy(ctx->err_event);
+  for (int k = 0; k < 4; ++k)
+    if (ctx->kt_ev[k]) cudaEventDestroy(ctx->kt_ev[k]);
+  delete ctx;
+}
+
+extern "C" const char* p3m_sr_last_error(const p3m_sr_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->last_error.c_str();
+}
+
+extern "C" p3m_status p3m_sr_sync(p3m_sr_ctx* ctx) {
+  if (!ctx) return P3M_ERR_INVALID;
+  p3m_status st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  if (st != P3M_OK) return st;
+  int bits = 0;
+  st = cuda_check(ctx, cudaMemcpy(&bits, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
+  if (st != P3M_OK) return st;
+  ctx->err_event_pending = false;
+  *ctx->err_host = bits;
+  return status_from_bits(ctx, bits);
+}
+
+extern "C" p3m_status p3m_sr_stats(p3m_sr_ctx* ctx, p3m_sr_stats_t* out) {
+  if (!ctx || !out) return P3M_ERR_INVALID;
+  p3m_status st = p3m_sr_sync(ctx);
+  std::memset(out, 0, sizeof(*out));
+  out->n_tile = ctx->geo.n_t;
+  for (int d = 0; d < 3; ++d) out->n_sub[d] = ctx->geo.ns[d];
+  out->n_subtiles = ctx->geo.S;
+  int small[3] = {0, 0, 0};
+  unsigned long long pc = 0;
+  cudaMemcpy(small, ctx->dev_small, sizeof(small), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&pc, ctx->pair_count, sizeof(pc), cudaMemcpyDeviceToHost);
+  out->n_chunks = ctx->pairs_built ? small[0] : 0;
+  out->n_active = ctx->pairs_built ? small[2] : 0;
+  out->pairs_last = (int64_t)pc;
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->kt_pending[k]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ctx->kt_ev[2 * k], ctx->kt_ev[2 * k + 1]) == cudaSuccess) ctx->kt_ms[k] = ms;
+      ctx->kt_pending[k] = false;
+    }
+  }
+  out->force_kernel_ms = ctx->kt_ms[0];
+  out->vjp_kernel_ms = ctx->kt_ms[1];
+  out->kernel_launches = ctx->launches;
+  return st;
+}

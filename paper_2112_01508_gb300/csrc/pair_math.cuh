@@ -1,0 +1,185 @@
+// The short-range pair bracket B(r) of Eq. p3m_gravity (Section 2.1.3) and its
+// derivative, in FP32 (fast path) and FP64 (parity path).
+//
+//   B(r) = erfc(u)/r^3 + exp(-u^2)/(sqrt(pi) x_s r^2) + ( |x|^{-3}_shape - r^{-3} ),
+//   u = r / (2 x_s).
+//
+// Main branch (r >= r_sw): B r^3 = exp(-u^2) [erfcx(u) + 2u/sqrt(pi)], i.e.
+//   B = exp(-u^2) r^{-2} [erfcx(u) r^{-1} + 1/(sqrt(pi) x_s)],
+// with exp(-u^2) from one ex2 and erfcx from the fit of fit_erfcx.py.
+// Softened branch (r < r_sw, rare): the exact identity
+//   erfc(u) + 2u/sqrt(pi) e^{-u^2} - 1 = -u^3 h(u),  h(u) = [erf u - 2u/sqrt(pi) e^{-u^2}] / u^3,
+// gives B = |x|^{-3}_shape - h(u) / (2 x_s)^3 without the cancellation of
+// erfc(u)/r^3 against -r^{-3}; h is its Taylor series in u^2.
+// Shapes (Section 2.1.1): Plummer (r^2+eps^2)^{-3/2} (Eq. plummer_shape) and
+// the B-spline piecewise polynomial of Eq. bspline_force (eps_B = 2.8 eps).
+#pragma once
+
+#include "common.cuh"
+
+namespace p3m {
+
+constexpr int kHTermsF = 8;
+constexpr int kHTermsD = 18;
+
+// Series coefficients of h(u) = sum_n H_n u^{2n} and h'(u)/u = sum_n Hd_n u^{2n}.
+struct SeriesConsts {
+  float h_f[kHTermsF], hd_f[kHTermsF];
+  double h_d[kHTermsD], hd_d[kHTermsD];
+};
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ---------------------------------------------------------------- FP32 ----
+
+// Main branch.  Returns B; with VJP also D = B'(r)/r.
+template <int SOFT, bool VJP>
+__device__ __forceinline__ float bracket_main_f32(float r2, const ForceConsts& f, float& D) {
+  float rinv = rsqrt_approx(r2);
+  float r = r2 * rinv;
+  float e = ex2_approx(r2 * f.ce_f);
+  float t = rcp_approx(fmaf(r, f.kc_f, 1.0f));
+  float q = fmaf(f.c_f[5], t, f.c_f[4]);
+  q = fmaf(q, t, f.c_f[3]);
+  q = fmaf(q, t, f.c_f[2]);
+  q = fmaf(q, t, f.c_f[1]);
+  q = fmaf(q, t, f.c_f[0]);
+  float ex = q * t;  // erfcx(u)
+  float rinv2 = rinv * rinv;
+  float er2 = e * rinv2;
+  float B = er2 * fmaf(ex, rinv, f.k2_f);
+  if (VJP) {
+    // g'(r)/r = -r^{-2} (3 g + exp(-u^2) / (2 sqrt(pi) x_s^3))
+    D = -rinv2 * fmaf(3.0f, B, e * f.k3_f);
+  }
+  if (SOFT == P3M_SOFT_PLUMMER) {
+    float p = rsqrt_approx(r2 + f.eps2_f);
+    float p3 = p * p * p;
+    float rinv3 = rinv2 * rinv;
+    if (VJP) D += 3.0f * (rinv3 * rinv2 - p3 * p * p);
+    B += p3 - rinv3;
+  }
+  return B;
+}
+
+// Softened branch, r^2 < r_sw^2 (and r = 0 for point particles).
+template <int SOFT, bool VJP>
+__device__ __forceinline__ float bracket_soft_f32(float r2, const ForceConsts& f, const SeriesConsts& sc,
+                                                  float& D) {
+  if (SOFT == P3M_SOFT_NONE) {  // only coincident particles arrive here: zero by convention
+    D = 0.0f;
+    return 0.0f;
+  }
+  float r = sqrtf(r2);
+  float u = r * f.inv2xs_f;
+  float u2 = u * u;
+  float h = sc.h_f[kHTermsF - 1];
+#pragma unroll
+  for (int k = kHTermsF - 2; k >= 0; --k) h = fmaf(h, u2, sc.h_f[k]);
+  float s3, ds;  // |x|^{-3}_shape and its r-derivative divided by r
+  if (SOFT == P3M_SOFT_BSPLINE) {
+    float x = r * f.inv_epsb_f;
+    float c = f.bnorm_f;
+    float ce = c * f.inv_epsb_f * f.inv_epsb_f;  // 32 / eps_B^5
+    if (x < 0.5f) {
+      s3 = c * fmaf(x * x, x - 1.2f, 1.0f / 3.0f);
+      ds = ce * fmaf(3.0f, x, -2.4f);
+    } else {
+      float xi = 1.0f / x;
+      float xi3 = xi * xi * xi;
+      s3 = c * (fmaf(x * x, fmaf(-1.0f / 3.0f, x, 1.2f), fmaf(-1.5f, x, 2.0f / 3.0f)) - xi3 * (1.0f / 480.0f));
+      ds = ce * (fmaf(-1.0f, x, 2.4f) - 1.5f * xi + xi3 * xi * xi * (1.0f / 160.0f));
+    }
+  } else {  // Plummer
+    float p = rsqrt_approx(r2 + f.eps2_f);
+    s3 = p * p * p;
+    ds = -3.0f * s3 * p * p;
+  }
+  if (VJP) {
+    float hd = sc.hd_f[kHTermsF - 1];
+#pragma unroll
+    for (int k = kHTermsF - 2; k >= 0; --k) hd = fmaf(hd, u2, sc.hd_f[k]);
+    // d/dr [h(u)/(2x_s)^3] / r = h'(u)/u / (2x_s)^5
+    D = ds - hd * f.hscale_f * f.inv2xs_f * f.inv2xs_f;
+  }
+  return s3 - h * f.hscale_f;
+}
+
+// ---------------------------------------------------------------- FP64 ----
+
+template <int SOFT, bool VJP>
+__device__ __forceinline__ double bracket_f64(double r2, const ForceConsts& f, const SeriesConsts& sc, double& D) {
+  const double inv_sqrt_pi = 0.56418958354775628695;
+  if (r2 < f.rsw2_d || r2 == 0.0) {
+    if (SOFT == P3M_SOFT_NONE) {
+      D = 0.0;
+      return 0.0;
+    }
+    double r = sqrt(r2);
+    double u = r / (2.0 * f.x_s);
+    double u2 = u * u;
+    double h = sc.h_d[kHTermsD - 1];
+    for (int k = kHTermsD - 2; k >= 0; --k) h = fma(h, u2, sc.h_d[k]);
+    double w = 2.0 * f.x_s;
+    double w3 = w * w * w;
+    double s3, ds;
+    if (SOFT == P3M_SOFT_BSPLINE) {
+      double eb = f.eps_b;
+      double x = r / eb;
+      double c = 32.0 / (eb * eb * eb);
+      double ce = c / (eb * eb);
+      if (x < 0.5) {
+        s3 = c * (x * x * x - 1.2 * x * x + 1.0 / 3.0);
+        ds = ce * (3.0 * x - 2.4);
+      } else {
+        s3 = c * (-x * x * x / 3.0 + 1.2 * x * x - 1.5 * x + 2.0 / 3.0 - 1.0 / (480.0 * x * x * x));
+        ds = ce * (-x + 2.4 - 1.5 / x + 1.0 / (160.0 * x * x * x * x * x));
+      }
+    } else {
+      double s = r2 + f.eps * f.eps;
+      double p = 1.0 / sqrt(s);
+      s3 = p * p * p;
+      ds = -3.0 * s3 / s;
+    }
+    if (VJP) {
+      double hd = sc.hd_d[kHTermsD - 1];
+      for (int k = kHTermsD - 2; k >= 0; --k) hd = fma(hd, u2, sc.hd_d[k]);
+      D = ds - hd / (w3 * w * w);
+    }
+    return s3 - h / w3;
+  }
+  double r = sqrt(r2);
+  double rinv = 1.0 / r;
+  double u = r / (2.0 * f.x_s);
+  double e = exp(-u * u);
+  double rinv3 = rinv * rinv * rinv;
+  double B = (erfc(u) + 2.0 * inv_sqrt_pi * u * e) * rinv3;
+  if (VJP) {
+    double k3 = inv_sqrt_pi / (2.0 * f.x_s * f.x_s * f.x_s);
+    D = -(3.0 * B + e * k3) * rinv * rinv;
+  }
+  if (SOFT == P3M_SOFT_PLUMMER) {
+    double s = r2 + f.eps * f.eps;
+    double p = 1.0 / sqrt(s);
+    double p3 = p * p * p;
+    if (VJP) D += -3.0 * p3 / s + 3.0 * rinv3 * rinv * rinv;
+    B += p3 - rinv3;
+  }
+  return B;
+}
+
+}  // namespace p3m

@@ -1,0 +1,232 @@
+// Sorting particles into tiles and subtiles (Section 2.1.3, "Tiles": an O(N)
+// sort into the box tiling, with the particles reordered in memory in the
+// tile -> subtile -> particle walk order of the short-range computation).
+//
+// GPU design: one pass bins every particle (subtile id from one correctly
+// rounded multiply per dimension) and builds the subtile histogram; an
+// exclusive scan turns it into the subtile offsets.  The permutation itself
+// comes from a stable LSD radix sort of the subtile ids (8-bit digits at
+// most, warp-level ranking with match.any so that equal ids keep their input
+// order), after which positions and any carried arrays are gathered.
+#include "ctx.cuh"
+
+namespace p3m {
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixWarps = kRadixThreads / kWarp;
+constexpr int kRadixSteps = 16;                           // items per lane
+constexpr int kRadixTile = kRadixThreads * kRadixSteps;   // 4096 items per block
+
+__global__ void k_bin(const double* __restrict__ pos, int64_t n, Geometry g, int* __restrict__ keys,
+                      int* __restrict__ vals, int* __restrict__ counts, int* __restrict__ err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int gc[3];
+  bool bad = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = pos[d * n + i];
+    bool ok = (v >= 0.0) && (v < g.box);  // false for NaN
+    bad |= !ok;
+    double p = __dmul_rn(ok ? v : 0.0, g.scale64[d]);
+    int q = (int)p;  // p >= 0: truncation is floor
+    gc[d] = q < g.M[d] - 1 ? q : g.M[d] - 1;
+  }
+  if (bad) atomicOr(err, kErrPosition);
+  int id = encode_subtile(g, gc[0], gc[1], gc[2]);
+  keys[i] = id;
+  vals[i] = (int)i;
+  atomicAdd(&counts[id], 1);
+}
+
+__global__ void k_radix_hist(const int* __restrict__ keys, int64_t n, int shift, int bits,
+                             int* __restrict__ hist, int nblocks) {
+  __shared__ int cnt[256];
+  const int radix = 1 << bits;
+  for (int d = threadIdx.x; d < radix; d += blockDim.x) cnt[d] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  const int mask = radix - 1;
+  for (int k = 0; k < kRadixSteps; ++k) {
+    int64_t i = base + (int64_t)k * kRadixThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & mask], 1);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < radix; d += blockDim.x) hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+}
+
+// Stable scatter of one radix pass.  Warp w of a block owns the contiguous
+// items [w*512, (w+1)*512) of the block's tile and walks them in 16 steps of
+// 32 consecutive items, so ranks follow the input order.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+    const int* __restrict__ keys_in, const int* __restrict__ vals_in, int* __restrict__ keys_out,
+    int* __restrict__ vals_out, int64_t n, int shift, int bits, const int* __restrict__ hist, int nblocks) {
+  __shared__ int wcnt[kRadixWarps][256];
+  const int radix = 1 << bits;
+  const int mask = radix - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = lane; d < radix; d += 32) wcnt[warp][d] = 0;
+  __syncwarp();
+  const int64_t wbase = (int64_t)blockIdx.x * kRadixTile + (int64_t)warp * (kRadixSteps * kWarp);
+  const unsigned lt = (1u << lane) - 1u;
+  int key[kRadixSteps], val[kRadixSteps], rank[kRadixSteps];
+#pragma unroll
+  for (int k = 0; k < kRadixSteps; ++k) {
+    int64_t i = wbase + k * kWarp + lane;
+    bool valid = i < n;
+    key[k] = valid ? keys_in[i] : 0;
+    val[k] = valid ? vals_in[i] : 0;
+    int d = (key[k] >> shift) & mask;
+    int tag = valid ? d : -1 - lane;  // invalid lanes match nobody
+    unsigned peers = __match_any_sync(0xffffffffu, tag);
+    int r = __popc(peers & lt);
+    int base = valid ? wcnt[warp][d] : 0;
+    __syncwarp();
+    if (valid && r == 0) wcnt[warp][d] = base + __popc(peers);
+    __syncwarp();
+    rank[k] = base + r;
+  }
+  __syncthreads();
+  // exclusive prefix over the warps of the block, per digit
+  for (int d = threadIdx.x; d < radix; d += blockDim.x) {
+    int run = 0;
+#pragma unroll
+    for (int w = 0; w < kRadixWarps; ++w) {
+      int t = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kRadixSteps; ++k) {
+    int64_t i = wbase + k * kWarp + lane;
+    if (i < n) {
+      int d = (key[k] >> shift) & mask;
+      int64_t dst = (int64_t)hist[(int64_t)d * nblocks + blockIdx.x] + wcnt[warp][d] + rank[k];
+      keys_out[dst] = key[k];
+      vals_out[dst] = val[k];
+    }
+  }
+}
+
+__global__ void k_gather_pos(const double* __restrict__ src, const int* __restrict__ perm, int64_t n,
+                             double* __restrict__ dst) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int64_t j = perm[k];
+  dst[k] = src[j];
+  dst[n + k] = src[n + j];
+  dst[2 * n + k] = src[2 * n + j];
+}
+
+template <class T>
+__global__ void k_gather_words(const T* __restrict__ src, const int* __restrict__ perm, int64_t n, int words,
+                               T* __restrict__ dst) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int64_t j = perm[k];
+  for (int w = 0; w < words; ++w) dst[k * words + w] = src[j * words + w];
+}
+
+static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static p3m_status gather_carry(p3m_sr_ctx* ctx, void* arr, int bytes) {
+  const int64_t n = ctx->n;
+  const int t = 256;
+  cudaStream_t s = ctx->stream;
+  uintptr_t a = (uintptr_t)arr;
+  if (bytes % 8 == 0 && a % 8 == 0)
+    k_gather_words<uint64_t><<<blocks_for(n, t), t, 0, s>>>((const uint64_t*)arr, ctx->perm, n, bytes / 8,
+                                                             (uint64_t*)ctx->gather_tmp);
+  else if (bytes % 4 == 0 && a % 4 == 0)
+    k_gather_words<uint32_t><<<blocks_for(n, t), t, 0, s>>>((const uint32_t*)arr, ctx->perm, n, bytes / 4,
+                                                             (uint32_t*)ctx->gather_tmp);
+  else if (bytes % 2 == 0 && a % 2 == 0)
+    k_gather_words<uint16_t><<<blocks_for(n, t), t, 0, s>>>((const uint16_t*)arr, ctx->perm, n, bytes / 2,
+                                                             (uint16_t*)ctx->gather_tmp);
+  else
+    k_gather_words<uint8_t><<<blocks_for(n, t), t, 0, s>>>((const uint8_t*)arr, ctx->perm, n, bytes,
+                                                            (uint8_t*)ctx->gather_tmp);
+  ++ctx->launches;
+  p3m_status st = cuda_check(ctx, cudaGetLastError(), "gather kernel");
+  if (st != P3M_OK) return st;
+  return cuda_check(ctx, cudaMemcpyAsync(arr, ctx->gather_tmp, (size_t)bytes * n, cudaMemcpyDeviceToDevice, s),
+                    "carry copy");
+}
+
+}  // namespace p3m
+
+using namespace p3m;
+
+extern "C" p3m_status p3m_sr_sort(p3m_sr_ctx* ctx, double* pos, void* const* carry, const int* carry_bytes,
+                                  int n_carry, int32_t* perm_out, int32_t* subtile_id_out) {
+  if (!ctx) return P3M_ERR_INVALID;
+  const int64_t n = ctx->n;
+  if (n_carry < 0 || (n_carry > 0 && (!carry || !carry_bytes)))
+    return fail(ctx, P3M_ERR_INVALID, "sort: bad carry arguments");
+  for (int c = 0; c < n_carry; ++c) {
+    if (carry_bytes[c] < 1 || carry_bytes[c] > 32) return fail(ctx, P3M_ERR_INVALID, "sort: carry_bytes must be 1..32");
+    if (!carry[c] && n > 0) return fail(ctx, P3M_ERR_INVALID, "sort: null carry array");
+  }
+  if (!pos && n > 0) return fail(ctx, P3M_ERR_INVALID, "sort: null positions");
+  p3m_status st = poll_latched(ctx);
+  if (st != P3M_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const Geometry& g = ctx->geo;
+  ctx->pairs_built = false;
+  ctx->all_chunks_built = false;
+  st = cuda_check(ctx, cudaMemsetAsync(ctx->offsets, 0, sizeof(int) * (g.S + 1), s), "memset offsets");
+  if (st != P3M_OK) return st;
+  if (n > 0) {
+    k_bin<<<blocks_for(n, 256), 256, 0, s>>>(pos, n, g, ctx->keys[0], ctx->vals[0], ctx->offsets, ctx->err_dev);
+    ++ctx->launches;
+    if ((st = cuda_check(ctx, cudaGetLastError(), "bin kernel")) != P3M_OK) return st;
+  }
+  st = cuda_check(ctx, scan_exclusive_i32(ctx->offsets, ctx->offsets, g.S + 1, ctx->scan_scratch, s, &ctx->launches), "scan");
+  if (st != P3M_OK) return st;
+
+  int cur = 0;
+  if (n > 0) {
+    const int nblocks = (int)((n + kRadixTile - 1) / kRadixTile);
+    int shift = 0;
+    for (int p = 0; p < ctx->radix_passes; ++p) {
+      int bits = ctx->radix_bits[p];
+      k_radix_hist<<<nblocks, kRadixThreads, 0, s>>>(ctx->keys[cur], n, shift, bits, ctx->hist, nblocks);
+      ++ctx->launches;
+      if ((st = cuda_check(ctx, cudaGetLastError(), "radix hist")) != P3M_OK) return st;
+      st = cuda_check(ctx, scan_exclusive_i32(ctx->hist, ctx->hist, (int64_t)nblocks << bits, ctx->scan_scratch, s, &ctx->launches),
+                      "radix scan");
+      if (st != P3M_OK) return st;
+      k_radix_scatter<<<nblocks, kRadixThreads, 0, s>>>(ctx->keys[cur], ctx->vals[cur], ctx->keys[cur ^ 1],
+                                                          ctx->vals[cur ^ 1], n, shift, bits, ctx->hist, nblocks);
+      ++ctx->launches;
+      if ((st = cuda_check(ctx, cudaGetLastError(), "radix scatter")) != P3M_OK) return st;
+      cur ^= 1;
+      shift += bits;
+    }
+  }
+  ctx->cell = ctx->keys[cur];
+  ctx->perm = ctx->vals[cur];
+  if (n > 0) {
+    double* tmp = (double*)ctx->gather_tmp;
+    k_gather_pos<<<blocks_for(n, 256), 256, 0, s>>>(pos, ctx->perm, n, tmp);
+    ++ctx->launches;
+    if ((st = cuda_check(ctx, cudaGetLastError(), "gather positions")) != P3M_OK) return st;
+    st = cuda_check(ctx, cudaMemcpyAsync(pos, tmp, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy");
+    if (st != P3M_OK) return st;
+    for (int c = 0; c < n_carry; ++c)
+      if ((st = gather_carry(ctx, carry[c], carry_bytes[c])) != P3M_OK) return st;
+    if (perm_out)
+      if ((st = cuda_check(ctx, cudaMemcpyAsync(perm_out, ctx->perm, sizeof(int) * n, cudaMemcpyDeviceToDevice, s),
+                           "perm copy")) != P3M_OK)
+        return st;
+    if (subtile_id_out)
+      if ((st = cuda_check(ctx, cudaMemcpyAsync(subtile_id_out, ctx->cell, sizeof(int) * n,
+                                                cudaMemcpyDeviceToDevice, s), "id copy")) != P3M_OK)
+        return st;
+  }
+  report_latched(ctx);
+  ctx->sorted = true;
+  return P3M_OK;
+}

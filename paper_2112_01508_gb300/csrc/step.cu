@@ -1,0 +1,149 @@
+// Rung assignment (Section 2.2.2, Eq. rung), kick and drift (Section 2.2.2,
+// operators K and D with a static scale factor a = 1).  All three are
+// elementwise and HBM-bound; the arithmetic is IEEE double with explicit
+// round-to-nearest intrinsics so that the integer rung decision and the
+// updated momenta/positions are reproducible bit for bit.
+#include <cmath>
+
+#include "ctx.cuh"
+
+namespace p3m {
+
+static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <class A>
+__global__ void k_rungs(const A* __restrict__ acc, int64_t n, double qq, int n_rung, int8_t* __restrict__ rung,
+                        int* __restrict__ err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double ax = (double)acc[i], ay = (double)acc[n + i], az = (double)acc[2 * n + i];
+  // s = q^2 (|a|^2) with |a|^2 = (ax*ax + ay*ay) + az*az, each op correctly rounded
+  double a2 = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
+  double s = __dmul_rn(qq, a2);
+  int l = 0;
+  if (isnan(s) || isinf(s)) {
+    atomicOr(err, kErrNonfiniteAcc);
+  } else {
+    double p = 1.0;
+    while (l < n_rung - 1 && s > p) {
+      p *= 16.0;
+      ++l;
+    }
+  }
+  rung[i] = (int8_t)l;
+}
+
+struct KickFactors {
+  double k[8];
+};
+
+template <class M, class A>
+__global__ void k_kick(M* __restrict__ mom, const A* __restrict__ acc, const int8_t* __restrict__ rung, int rung_min,
+                       int64_t n, KickFactors kf) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double k = kf.k[0];
+  if (rung) {
+    int l = rung[i];
+    if (l < rung_min) return;
+    k = kf.k[l < 0 ? 0 : (l > 7 ? 7 : l)];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double q = (double)mom[d * n + i];
+    double v = __dadd_rn(q, __dmul_rn((double)acc[d * n + i], k));
+    mom[d * n + i] = (M)v;
+  }
+}
+
+template <class M>
+__global__ void k_drift(double* __restrict__ pos, const M* __restrict__ mom, int64_t n, double factor, double box) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = __dadd_rn(pos[d * n + i], __dmul_rn((double)mom[d * n + i], factor));
+    v = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
+    if (v >= box || v < 0.0) v = 0.0;
+    pos[d * n + i] = v;
+  }
+}
+
+}  // namespace p3m
+
+using namespace p3m;
+
+extern "C" p3m_status p3m_sr_assign_rungs(p3m_sr_ctx* ctx, const void* acc, int acc_precision, double dt, double eta,
+                                          double eps, int8_t* rung_out) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (acc_precision != 32 && acc_precision != 64) return fail(ctx, P3M_ERR_INVALID, "assign_rungs: bad precision");
+  if (ctx->n > 0 && (!acc || !rung_out)) return fail(ctx, P3M_ERR_INVALID, "assign_rungs: null pointer");
+  if (!(dt >= 0.0) || !(eta > 0.0) || !(eps > 0.0))
+    return fail(ctx, P3M_ERR_INVALID, "assign_rungs: need dt >= 0, eta > 0, eps > 0");
+  p3m_status st = poll_latched(ctx);
+  if (st != P3M_OK) return st;
+  if (ctx->n == 0) return P3M_OK;
+  // q = dt^2 / (2 eta eps), evaluated in this order in IEEE double
+  volatile double t1 = dt * dt;
+  volatile double t2 = 2.0 * eta;
+  volatile double t3 = t2 * eps;
+  volatile double q = t1 / t3;
+  double qq = q * q;
+  const int t = 256;
+  if (acc_precision == 64)
+    { k_rungs<double><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>((const double*)acc, ctx->n, qq, ctx->prm.n_rung,
+                                                                   rung_out, ctx->err_dev); ++ctx->launches; }
+  else
+    { k_rungs<float><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>((const float*)acc, ctx->n, qq, ctx->prm.n_rung,
+                                                                  rung_out, ctx->err_dev); ++ctx->launches; }
+  if ((st = cuda_check(ctx, cudaGetLastError(), "rung kernel")) != P3M_OK) return st;
+  report_latched(ctx);
+  return P3M_OK;
+}
+
+extern "C" p3m_status p3m_sr_kick(p3m_sr_ctx* ctx, void* mom, int mom_precision, const void* acc, int acc_precision,
+                                  const int8_t* rung, int rung_min, const double* kick_factor) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if ((mom_precision != 32 && mom_precision != 64) || (acc_precision != 32 && acc_precision != 64))
+    return fail(ctx, P3M_ERR_INVALID, "kick: precision must be 32 or 64");
+  if (!kick_factor) return fail(ctx, P3M_ERR_INVALID, "kick: null kick_factor");
+  if (ctx->n > 0 && (!mom || !acc)) return fail(ctx, P3M_ERR_INVALID, "kick: null pointer");
+  p3m_status st = poll_latched(ctx);
+  if (st != P3M_OK) return st;
+  if (ctx->n == 0) return P3M_OK;
+  KickFactors kf{};
+  for (int l = 0; l < ctx->prm.n_rung; ++l) kf.k[l] = kick_factor[l];
+  const int t = 256;
+  const unsigned b = blocks_for(ctx->n, t);
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  if (mom_precision == 64 && acc_precision == 32)
+    { k_kick<double, float><<<b, t, 0, s>>>((double*)mom, (const float*)acc, rung, rung_min, n, kf); ++ctx->launches; }
+  else if (mom_precision == 64 && acc_precision == 64)
+    { k_kick<double, double><<<b, t, 0, s>>>((double*)mom, (const double*)acc, rung, rung_min, n, kf); ++ctx->launches; }
+  else if (mom_precision == 32 && acc_precision == 32)
+    { k_kick<float, float><<<b, t, 0, s>>>((float*)mom, (const float*)acc, rung, rung_min, n, kf); ++ctx->launches; }
+  else
+    { k_kick<float, double><<<b, t, 0, s>>>((float*)mom, (const double*)acc, rung, rung_min, n, kf); ++ctx->launches; }
+  return cuda_check(ctx, cudaGetLastError(), "kick kernel");
+}
+
+extern "C" p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom, int mom_precision, double factor) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (mom_precision != 32 && mom_precision != 64) return fail(ctx, P3M_ERR_INVALID, "drift: bad precision");
+  if (ctx->n > 0 && (!pos || !mom)) return fail(ctx, P3M_ERR_INVALID, "drift: null pointer");
+  if (!std::isfinite(factor)) return fail(ctx, P3M_ERR_INVALID, "drift: factor must be finite");
+  p3m_status st = poll_latched(ctx);
+  if (st != P3M_OK) return st;
+  if (ctx->n == 0) return P3M_OK;
+  const int t = 256;
+  if (mom_precision == 64)
+    { k_drift<double><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>(pos, (const double*)mom, ctx->n, factor,
+                                                                  ctx->prm.box); ++ctx->launches; }
+  else
+    { k_drift<float><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>(pos, (const float*)mom, ctx->n, factor,
+                                                                 ctx->prm.box); ++ctx->launches; }
+  ctx->pairs_built = false;  // positions moved: the tiling must be rebuilt
+  ctx->sorted = false;
+  return cuda_check(ctx, cudaGetLastError(), "drift kernel");
+}

@@ -1,0 +1,75 @@
+"""CPU-only checks of the C-ABI library: it builds, loads and exports every
+symbol declared in include/*.h, and host-side validation works without a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2112_01508_gb300 import _native as nat
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(p3m_\w+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = nat.load()
+    declared = _declared_functions()
+    assert declared, "no declarations found"
+    missing = [s for s in declared if not hasattr(lib, s)]
+    assert not missing, missing
+    assert set(nat.EXPORTS) == declared
+
+
+def _params(**kw):
+    p = nat.P3MParams()
+    p.n, p.box, p.x_s, p.x_r, p.G_m = 1000, 1.0, 0.01, 0.045, 1e-3
+    p.softening, p.eps, p.n_rung = 2, 1e-3, 8
+    p.n_sub[0] = p.n_sub[1] = p.n_sub[2] = 2
+    for k, v in kw.items():
+        if k == "n_sub":
+            p.n_sub[0], p.n_sub[1], p.n_sub[2] = v
+        else:
+            setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(x_r=0.3), nat.P3M_ERR_TOO_FEW_TILES),     # floor(1/0.3) = 3 tiles < 4
+    (dict(n=-1), nat.P3M_ERR_INVALID),
+    (dict(box=0.0), nat.P3M_ERR_INVALID),
+    (dict(x_s=-1.0), nat.P3M_ERR_INVALID),
+    (dict(softening=3), nat.P3M_ERR_INVALID),
+    (dict(eps=0.0), nat.P3M_ERR_INVALID),
+    (dict(n_sub=(0, 2, 2)), nat.P3M_ERR_INVALID),
+    (dict(n_rung=9), nat.P3M_ERR_INVALID),
+    (dict(eps=0.05), nat.P3M_ERR_INVALID),           # softening beyond 2 x_s
+])
+def test_create_rejects_bad_parameters(kw, status):
+    st, ctx = nat.p3m_sr_create(_params(**kw), 0)
+    assert st == status
+    assert not ctx.value
+
+
+def test_null_context_is_rejected():
+    lib = nat.load()
+    assert lib.p3m_sr_sync(None) == nat.P3M_ERR_INVALID
+    assert lib.p3m_sr_forces(None, None, 32, None) == nat.P3M_ERR_INVALID
+    assert lib.p3m_sr_last_error(None) == b"null context"
+    lib.p3m_sr_destroy(None)
+
+
+def test_header_documents_every_entry_point():
+    text = open(os.path.join(ROOT, "include", "p3m_sr.h")).read()
+    for name in nat.EXPORTS:
+        assert name in text
+    assert "Section 2.1.3" in text and "Eq. rung" in text

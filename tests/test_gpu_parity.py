@@ -1,0 +1,149 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests._gpu_helpers import gpu_forces, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+W1 = synth.workload("n32k")
+FP64_TOL = 1e-12   # relative RMS force, FP64 path
+FP32_TOL = 1e-5    # relative RMS force, FP32 path
+
+
+@pytest.fixture(scope="module")
+def n32k():
+    pos = synth.workload_positions(W1)
+    refs = {}
+    for soft in ("none", "plummer", "bspline"):
+        refs[soft] = oracle.sr_accel(pos, W1.x_s, W1.x_r, W1.G_m, soft, W1.eps)
+    return pos, refs
+
+
+@pytest.mark.parametrize("softening", ["none", "plummer", "bspline"])
+def test_n32k_fp64(n32k, softening):
+    pos, refs = n32k
+    ref, pairs = refs[softening]
+    r = gpu_forces(pos, W1.x_s, W1.x_r, W1.G_m, softening, W1.eps, precision=64)
+    assert r["pairs"] == pairs
+    assert rel_rms(r["acc"], ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("softening", ["plummer", "bspline"])
+def test_n32k_fp32(n32k, softening):
+    pos, refs = n32k
+    ref, pairs = refs[softening]
+    r = gpu_forces(pos, W1.x_s, W1.x_r, W1.G_m, softening, W1.eps, precision=32)
+    # pairs within a few ulp of the cutoff may be decided differently in FP32
+    assert abs(r["pairs"] - pairs) <= max(2, 1e-6 * pairs)
+    assert rel_rms(r["acc"], ref) <= FP32_TOL
+
+
+def test_n32k_fp32_unsoftened_reported(n32k):
+    # point particles: FP32 error is reported, not bounded by 1e-5 (close pairs)
+    pos, refs = n32k
+    ref, _ = refs["none"]
+    r = gpu_forces(pos, W1.x_s, W1.x_r, W1.G_m, "none", 0.0, precision=32)
+    err = rel_rms(r["acc"], ref)
+    print("FP32 unsoftened rel RMS", err)
+    assert err < 1e-3
+
+
+def test_sort_bitexact_and_stable():
+    pos = synth.workload_positions(W1)
+    n = pos.shape[1]
+    from paper_2112_01508_gb300 import ShortRange
+    sr = ShortRange.from_workload(W1)
+    p = torch.from_numpy(pos.copy()).cuda()
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    tag = torch.arange(n, dtype=torch.int64, device="cuda")
+    sr.sort(p, carry=[tag], perm_out=perm, subtile_id_out=ids)
+    sr.sync()
+    perm_np = perm.cpu().numpy()
+    ids_np = ids.cpu().numpy()
+    ref_ids = oracle.subtile_ids(pos, sr.stats().n_tile, W1.n_sub)
+    np.testing.assert_array_equal(np.sort(perm_np), np.arange(n))
+    np.testing.assert_array_equal(ids_np, ref_ids[perm_np])
+    np.testing.assert_array_equal(p.cpu().numpy(), pos[:, perm_np])
+    np.testing.assert_array_equal(tag.cpu().numpy(), perm_np)
+    # stable: ids non-decreasing, and within equal ids the original order increases
+    assert np.all(np.diff(ids_np) >= 0)
+    same = np.diff(ids_np) == 0
+    assert np.all(np.diff(perm_np)[same] > 0)
+    # identical to a stable CPU sort of the oracle ids
+    np.testing.assert_array_equal(perm_np, np.argsort(ref_ids, kind="stable"))
+    sr.close()
+
+
+@pytest.mark.parametrize("rung_min", [0, 3, 7])
+def test_active_rungs(n32k, rung_min):
+    pos, _ = n32k
+    n = pos.shape[1]
+    rung = synth.uniform_int8(n, 77, 0, 8)
+    ref, pairs = oracle.sr_accel(pos, W1.x_s, W1.x_r, W1.G_m, "bspline", W1.eps, rung=rung, rung_min=rung_min)
+    act = rung >= rung_min
+    for prec, tol in ((64, FP64_TOL), (32, FP32_TOL)):
+        r = gpu_forces(pos, W1.x_s, W1.x_r, W1.G_m, "bspline", W1.eps, precision=prec, rung=rung,
+                       rung_min=rung_min)
+        assert np.all(np.isnan(r["acc"][:, ~act])), "inactive rows must be untouched"
+        assert rel_rms(r["acc"][:, act], ref[:, act]) <= tol
+        assert r["stats"].n_active == act.sum()
+        if prec == 64:
+            assert r["pairs"] == pairs
+
+
+@pytest.mark.parametrize("n_sub", [1, 2, 3, 4, (1, 2, 3)])
+def test_subtile_invariance(n32k, n_sub):
+    pos, refs = n32k
+    ref, pairs = refs["bspline"]
+    r64 = gpu_forces(pos, W1.x_s, W1.x_r, W1.G_m, "bspline", W1.eps, precision=64, n_sub=n_sub)
+    assert r64["pairs"] == pairs
+    assert rel_rms(r64["acc"], ref) <= FP64_TOL
+    r32 = gpu_forces(pos, W1.x_s, W1.x_r, W1.G_m, "bspline", W1.eps, precision=32, n_sub=n_sub)
+    assert rel_rms(r32["acc"], ref) <= FP32_TOL
+
+
+def _edge_case(pos, x_r=0.1, soft="bspline", eps=0.004):
+    x_s = x_r / 4.5
+    n = pos.shape[1]
+    ref, pairs = oracle.sr_accel(pos, x_s, x_r, 1.0 / max(n, 1), soft, eps)
+    for prec, tol in ((64, FP64_TOL), (32, FP32_TOL)):
+        r = gpu_forces(pos, x_s, x_r, 1.0 / max(n, 1), soft, eps, precision=prec)
+        if n:
+            assert rel_rms(r["acc"], ref) <= tol if np.abs(ref).sum() > 0 else np.all(r["acc"] == 0)
+        if prec == 64:
+            assert r["pairs"] == pairs
+
+
+def test_edge_tiny_and_empty():
+    _edge_case(np.zeros((3, 0)))
+    _edge_case(np.array([[0.5], [0.5], [0.5]]))
+    _edge_case(np.array([[0.5, 0.52], [0.5, 0.5], [0.5, 0.5]]))
+
+
+def test_edge_dense_cluster_and_boundaries():
+    rng = np.random.default_rng(3)
+    dense = 0.3 + 1e-3 * rng.normal(size=(3, 3000))          # one subtile holds everything
+    corner = (rng.random((3, 500)) * 0.02 - 0.01) % 1.0        # straddles all periodic faces
+    edge = np.array([[0.0, 1 - 2.0 ** -40, 0.5, 0.0], [0.0, 1 - 2.0 ** -40, 1e-17, 0.999999],
+                     [0.0, 1 - 2.0 ** -40, 0.5, 0.5]])
+    pos = np.concatenate([dense, corner, edge], axis=1)
+    _edge_case(pos)
+
+
+@pytest.mark.parametrize("count", [31, 32, 33, 63, 64, 65, 1000])
+def test_edge_ragged_chunks(count):
+    rng = np.random.default_rng(count)
+    pos = 0.5 + 0.01 * rng.random((3, count))  # all in one tile
+    _edge_case(pos)
+
+
+def test_coincident_particles():
+    rng = np.random.default_rng(9)
+    pos = rng.random((3, 400))
+    pos = np.concatenate([pos, pos[:, :50]], axis=1)  # 50 exact duplicates
+    _edge_case(pos)
