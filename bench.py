@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark of the short-range P3M hot path on GB300.
+
+One step = one pass of the whole forward hot path over the 128^3 clustered
+particle set (30% uniform + 70% in 4096 Plummer spheres, PM grid 256^3,
+x_s = 1.25/256, x_r = 4.5 x_s, B-spline softening), all particles active:
+
+  sort into tiles/subtiles (momenta and rungs carried) -> receiver work list
+  -> FP32 short-range accelerations -> rung assignment -> kick -> drift
+
+Reported value: interacting ordered pairs (i active, j != i, r < x_r) per
+second of device time.  Also reported: the FP64 path's rate, the adjoint
+(VJP) kernel time over the forward kernel time, the pair kernel's fraction of
+the FP32 ALU roofline, an end-to-end figure through host buffers, and the CPU
+oracle on a bounded sample of receivers.
+
+Usage:  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run; ranks run independent replicas
+(distinct seeds) and the value is the sum over ranks divided by the slowest
+rank's time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "short-range pair-interactions/s (FP32 vs FP64 path) at ≤1e-5 rel RMS force; adjoint time/fwd"
+UNIT = "pair-interactions/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+OPS_PER_PAIR = 26  # FP32 pipe instructions per interacting pair fixed for the roofline
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="n2m")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="receivers in the CPU-oracle sample")
+    ap.add_argument("--ref-sample", type=int, default=1 << 14, help="receivers per reference-arm step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["forces32", "forces64", "vjp32", "sort"], default=None,
+                    help="profiling mode: run just one kernel family (no contract line)")
+    return ap.parse_args()
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+FORCE_SOURCES = ["paper_2112_01508_gb300/csrc/force.cu", "paper_2112_01508_gb300/csrc/pair_math.cuh",
+                 "paper_2112_01508_gb300/csrc/common.cuh"]
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        power = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        loaded = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_rate(w, pos, n_recv: int, seed: int = 7):
+    """The CPU oracle as it stands, on a bounded sample of receivers (all suppliers)."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    recv = np.sort(rng.choice(w.n, size=min(n_recv, w.n), replace=False))
+    t0 = time.perf_counter()
+    _, pairs = oracle.sr_accel_subset(pos, recv, w.x_s, w.x_r, w.G_m, "bspline", w.eps)
+    dt = time.perf_counter() - t0
+    return float(pairs.sum()) / dt, dt, int(pairs.sum()), len(recv), oracle.num_threads()
+
+
+def traffic_from_profiles():
+    """DRAM traffic of the pair kernel from the committed ncu summary, if it was
+    captured on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "force_f32_n2m.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("source_hash") != source_hash(FORCE_SOURCES):
+            return None
+        return d.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2112_01508_gb300 import ShortRange
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    w = synth.workload(args.workload)
+    n = w.n
+    seed = w.seed + 1000 * rank  # independent replica per rank
+    pos_np = synth.positions(n, seed, w.frac_uniform, w.n_spheres, w.b_lo, w.b_hi)
+    pos_host = torch.from_numpy(pos_np).pin_memory()
+    mom_host = torch.zeros((3, n), dtype=torch.float64).pin_memory()
+    acc_host = torch.empty((3, n), dtype=torch.float32).pin_memory()
+    pos = pos_host.to(dev)
+    pos0 = pos.clone()
+    mom = torch.zeros((3, n), dtype=torch.float64, device=dev)
+    rung = torch.zeros(n, dtype=torch.int8, device=dev)
+    acc = torch.zeros((3, n), dtype=torch.float32, device=dev)
+    acc64 = torch.zeros((3, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    sr = ShortRange.from_workload(w, device=dev)
+    eta, n_rung = 0.025, 8
+
+    # time step from the fake kick (Section 2.2.2): 1% of particles on the top rung
+    sr.sort(pos)
+    sr.build_pairs()
+    sr.forces(pos, 64, acc64)
+    amag = torch.linalg.vector_norm(acc64, dim=0)
+    q99 = float(torch.quantile(amag[torch.randperm(n, device=dev)[:1 << 20]].float(), 0.99))
+    dt = 64.0 * (2.0 * eta * w.eps / max(q99, 1e-30)) ** 0.5
+    kick_factor = [dt / 2 ** l for l in range(n_rung)]
+    drift_factor = dt / 2 ** (n_rung - 1)
+
+    def step():
+        sr.sort(pos, carry=[mom, rung])
+        sr.build_pairs()
+        sr.forces(pos, 32, acc)
+        sr.assign_rungs(acc, dt, eta, w.eps, rung)
+        sr.kick(mom, acc, kick_factor, rung, 0)
+        sr.drift(pos, mom, drift_factor)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip().isdigit()]
+    sampler = ClockSampler(int(vis[local]) if local < len(vis) else local)
+    launches0 = sr.stats().kernel_launches
+    step_ms, kern_ms, pairs = [], [], []
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    torch.cuda.nvtx.range_push("timed")
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        st = sr.stats()  # synchronises the stream
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(st.force_kernel_ms)
+        pairs.append(st.pairs_last)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    launches = sr.stats().kernel_launches - launches0
+
+    total_ms_local = sum(step_ms)
+    total_ms = max_over_ranks(total_ms_local, world)
+    total_pairs = sum_over_ranks(float(sum(pairs)), world)
+    value = total_pairs / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    # dominant kernel: the FP32 pair kernel, timed live with events around its launch
+    kern_avg_ms = statistics.mean(kern_ms)
+    pairs_avg = statistics.mean(pairs)
+    achieved = pairs_avg / (kern_avg_ms * 1e-3)
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / OPS_PER_PAIR
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+                "frac": achieved / peak, "traffic": traffic_from_profiles(),
+                "kernel": "k_traverse<float, fwd, bspline>", "kernel_ms": kern_avg_ms,
+                "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz / "
+                              f"{OPS_PER_PAIR} FP32 ops per pair"}
+
+    # FP64 path and adjoint on the same (current) particle state
+    sr.sort(pos, carry=[mom, rung])
+    sr.build_pairs()
+    fp64_ms = []
+    for _ in range(3):
+        flush.zero_()
+        sr.forces(pos, 64, acc64)
+        fp64_ms.append(sr.stats().force_kernel_ms)
+    fp64_pairs = sr.stats().pairs_last
+    fwd_ms, vjp_ms = [], []
+    abar = torch.randn((3, n), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        flush.zero_()
+        sr.forces(pos, 32, acc)
+        fwd_ms.append(sr.stats().force_kernel_ms)
+        flush.zero_()
+        sr.vjp(pos, abar, 32)
+        vjp_ms.append(sr.stats().vjp_kernel_ms)
+    a32 = acc.double()
+    parity_32_64 = float(torch.sqrt(((a32 - acc64) ** 2).sum() / (acc64 ** 2).sum()))
+    fp64_rate = fp64_pairs / (statistics.mean(fp64_ms) * 1e-3)
+
+    # end to end through the public API with host buffers
+    e2e_ms, e2e_pairs = [], []
+    pos_host.copy_(pos0.cpu())
+    mom_host.zero_()
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pos.copy_(pos_host, non_blocking=True)
+        mom.copy_(mom_host, non_blocking=True)
+        step()
+        acc_host.copy_(acc, non_blocking=True)
+        e1.record(stream)
+        st = sr.stats()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+            e2e_pairs.append(st.pairs_last)
+    e2e_total = max_over_ranks(sum(e2e_ms), world)
+    e2e_value = sum_over_ranks(float(sum(e2e_pairs)), world) / (e2e_total * 1e-3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs, cp, nrecv, cores = cpu_oracle_rate(w, pos_np, args.cpu_sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{nrecv} seeded receivers of the {w.n}-particle set (all suppliers), {cp} pairs, "
+                         f"{secs:.1f} s wall"}
+
+    sr.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.description}", "n": n, "n_sub": w.n_sub,
+                       "softening": "bspline", "precision": "fp32 forces, fp64 positions/kicks",
+                       "step": "sort+carry, work list, FP32 forces, rungs, kick, drift (all active)",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "pairs_per_step": pairs_avg,
+            "fp64": {"value": fp64_rate, "unit": UNIT, "kernel_ms": statistics.mean(fp64_ms)},
+            "fp32_over_fp64": achieved / fp64_rate,
+            "fp32_vs_fp64_rel_rms": parity_32_64,
+            "adjoint_over_forward": statistics.mean(vjp_ms) / statistics.mean(fwd_ms),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * 8 * n,
+                    "d2h_bytes_per_step": 3 * 4 * n},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_only(args):
+    """Profiling mode: sort once, then repeat one entry point (for ncu captures)."""
+    import torch
+
+    import synth
+    from paper_2112_01508_gb300 import ShortRange
+
+    dev = torch.device("cuda", 0)
+    w = synth.workload(args.workload)
+    pos = torch.from_numpy(synth.workload_positions(w)).to(dev)
+    sr = ShortRange.from_workload(w, device=dev)
+    sr.sort(pos)
+    sr.build_pairs()
+    acc32 = torch.zeros((3, w.n), dtype=torch.float32, device=dev)
+    acc64 = torch.zeros((3, w.n), dtype=torch.float64, device=dev)
+    abar = torch.randn((3, w.n), dtype=torch.float32, device=dev)
+    times = []
+    for k in range(args.warmup + args.steps):
+        if args.only == "forces32":
+            sr.forces(pos, 32, acc32)
+        elif args.only == "forces64":
+            sr.forces(pos, 64, acc64)
+        elif args.only == "vjp32":
+            sr.vjp(pos, abar, 32)
+        else:
+            sr.sort(pos)
+        st = sr.stats()
+        if k >= args.warmup:
+            times.append(st.vjp_kernel_ms if args.only == "vjp32" else st.force_kernel_ms)
+    print(json.dumps({"only": args.only, "workload": w.name, "kernel_ms": times, "pairs": st.pairs_last}))
+    sr.close()
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands on the host cores."""
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = synth.workload(args.workload)
+    pos = synth.workload_positions(w)
+    ts, ps = [], []
+    cores = 1
+    for k in range(args.warmup + args.steps):
+        rate, secs, pairs, nrecv, cores = cpu_oracle_rate(w, pos, args.ref_sample, seed=100 + k)
+        if k >= args.warmup:
+            ts.append(secs)
+            ps.append(pairs)
+    value = sum(ps) / sum(ts)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{w.name}: {w.description}", "n": w.n, "softening": "bspline"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.ref_sample} seeded receivers per step, all {w.n} suppliers"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.only:
+        run_only(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

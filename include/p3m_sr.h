@@ -139,6 +139,20 @@ p3m_status p3m_sr_sort(p3m_sr_ctx* ctx, double* pos, void* const* carry, const i
                        int n_carry, int32_t* perm_out, int32_t* subtile_id_out);
 
 /*
+ * Move per-particle data between the caller's order and the order of the last
+ * p3m_sr_sort (the tile -> subtile walk order of Section 2.1.3), for data that
+ * was not carried through the sort (for example to return accelerations in the
+ * caller's order, or to bring gradients into the sorted order).
+ *   src, dst    distinct device arrays of `rows` rows of n elements of
+ *               elem_bytes bytes (1, 2, 4 or 8); a 3 x n SoA vector has rows = 3.
+ *   p3m_sr_permute:    dst[r][k] = src[r][perm[k]]   (caller order -> sorted)
+ *   p3m_sr_unpermute:  dst[r][perm[k]] = src[r][k]   (sorted -> caller order)
+ * with perm the permutation of the last sort (P3M_ERR_STATE before any sort).
+ */
+p3m_status p3m_sr_permute(p3m_sr_ctx* ctx, const void* src, void* dst, int elem_bytes, int rows);
+p3m_status p3m_sr_unpermute(p3m_sr_ctx* ctx, const void* src, void* dst, int elem_bytes, int rows);
+
+/*
  * Build the receiver set and work list for the following forces / vjp calls
  * (Section 2.1.3 "precomputed (sub)tile pairings"; Section 2.2.2: receivers are
  * the particles on rungs >= rung_min, suppliers are all particles).

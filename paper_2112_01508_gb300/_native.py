@@ -33,6 +33,7 @@ SOFTENING = {"none": 0, "plummer": 1, "bspline": 2}
 EXPORTS = (
     "p3m_sr_create", "p3m_sr_destroy", "p3m_sr_last_error", "p3m_sr_sync", "p3m_sr_stats", "p3m_sr_sort",
     "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
+    "p3m_sr_permute", "p3m_sr_unpermute",
 )
 
 
@@ -114,6 +115,10 @@ def load() -> ctypes.CDLL:
         L.p3m_sr_drift.restype = i
         L.p3m_sr_vjp.argtypes = [p, p, i, p, p]
         L.p3m_sr_vjp.restype = i
+        L.p3m_sr_permute.argtypes = [p, p, p, i, i]
+        L.p3m_sr_permute.restype = i
+        L.p3m_sr_unpermute.argtypes = [p, p, p, i, i]
+        L.p3m_sr_unpermute.restype = i
         _lib = L
         return L
 
@@ -179,3 +184,12 @@ def p3m_sr_drift(ctx, pos_ptr, mom_ptr, mom_precision, factor) -> int:
 def p3m_sr_vjp(ctx, pos_ptr, precision, acc_bar_ptr, pos_bar_ptr) -> int:
     return load().p3m_sr_vjp(ctx, ctypes.c_void_p(pos_ptr), int(precision), ctypes.c_void_p(acc_bar_ptr),
                              ctypes.c_void_p(pos_bar_ptr))
+
+
+def p3m_sr_permute(ctx, src_ptr, dst_ptr, elem_bytes, rows) -> int:
+    return load().p3m_sr_permute(ctx, ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr), int(elem_bytes), int(rows))
+
+
+def p3m_sr_unpermute(ctx, src_ptr, dst_ptr, elem_bytes, rows) -> int:
+    return load().p3m_sr_unpermute(ctx, ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr), int(elem_bytes),
+                                   int(rows))

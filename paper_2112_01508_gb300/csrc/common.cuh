@@ -89,6 +89,19 @@ __device__ __forceinline__ int encode_subtile(const Geometry& g, int gx, int gy,
   return tile * g.nsub3 + (sx * g.ns[1] + sy) * g.ns[2] + sz;
 }
 
+// ---- kernels of sort.cu launched from other translation units ---------------
+constexpr int kRadixThreadsPublic = 256;
+constexpr int kRadixTilePublic = 4096;  // items per radix block
+__global__ void k_bin(const double* __restrict__ pos, int64_t n, Geometry g, int* __restrict__ keys,
+                      int* __restrict__ vals, int* __restrict__ counts, int* __restrict__ err);
+__global__ void k_radix_hist(const int* __restrict__ keys, int64_t n, int shift, int bits, int* __restrict__ hist,
+                             int nblocks);
+__global__ void k_radix_scatter(const int* __restrict__ keys_in, const int* __restrict__ vals_in,
+                                int* __restrict__ keys_out, int* __restrict__ vals_out, int64_t n, int shift,
+                                int bits, const int* __restrict__ hist, int nblocks);
+__global__ void k_gather_pos(const double* __restrict__ src, const int* __restrict__ perm, int64_t n,
+                             double* __restrict__ dst);
+
 // ---- launch helpers (host) --------------------------------------------------
 
 // Exclusive scan of n int32 values (in may equal out).  Returns cudaError.

@@ -81,3 +81,8 @@ void report_latched(p3m_sr_ctx* ctx);
 p3m_status ensure_all_chunks(p3m_sr_ctx* ctx);
 
 }  // namespace p3m
+
+// Parameter checks and derived constants of p3m_sr_create (host.cu).
+p3m_status validate_params(p3m_sr_ctx* ctx, const p3m_sr_params& p);
+void setup_geometry(p3m_sr_ctx* ctx);
+void setup_force_consts(p3m_sr_ctx* ctx);

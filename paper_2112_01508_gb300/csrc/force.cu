@@ -8,21 +8,25 @@
 // order.  Receivers are the particles on active rungs (Section 2.2.2).
 //
 // GB300 design: the work unit is a receiver chunk -- up to 32 consecutive
-// receivers of one tile, one per warp lane.  A warp owns a chunk and:
+// receivers of one row of tiles (spanning at most four tiles along z), one per
+// warp lane.  A warp owns a chunk and:
 //   1. builds the chunk's frame (origin: the subtile of its first receiver)
-//      and tight bounding box;
+//      and the receivers' tight bounding box;
 //   2. enumerates, 32 candidates at a time across the lanes, the subtiles of
 //      the blocky ball around the chunk's subtile block (the paper's subtile
 //      pairing generalised to a block of subtiles), keeps those whose box gap
-//      to the chunk's bounding box is below x_r, and appends their particle
-//      ranges to a per-warp list in shared memory;
+//      to the bounding box is below x_r, and appends their particle ranges to
+//      a per-warp list in shared memory;
 //   3. walks the concatenated supplier ranges 32 at a time: each lane loads
 //      one supplier j (FP32 coordinates relative to its subtile origin, moved
-//      into the chunk frame by the integer subtile offset), tests it against
-//      the chunk's bounding box, and the survivors are broadcast to all lanes
-//      with warp shuffles, where every lane evaluates its own (i, j) pair.
-// Chunks are handed out dynamically through an atomic counter (persistent
-// warps), which balances the strongly varying cost of clustered regions.
+//      into the chunk frame by the integer subtile offset) and tests it against
+//      the bounding box; the survivors are broadcast to all lanes, and every
+//      lane evaluates its own (i, j) pair.
+// The FP32 forward kernel stages the survivors in shared memory as packed
+// pairs and evaluates two suppliers per step in f32x2 arithmetic; the FP64
+// forward and the adjoint broadcast survivors with warp shuffles.  Chunks are
+// handed out through an atomic counter to persistent warps, which balances the
+// strongly varying cost of clustered regions.
 #include <algorithm>
 #include <cmath>
 
@@ -34,7 +38,10 @@ namespace p3m {
 
 constexpr int kForceThreads = 128;
 constexpr int kForceWarps = kForceThreads / kWarp;
-constexpr int kListCap = 128;  // supplier subtiles buffered per warp
+#ifndef P3M_LISTCAP
+#define P3M_LISTCAP 128
+#endif
+constexpr int kListCap = P3M_LISTCAP;  // supplier subtiles buffered per warp
 
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -50,9 +57,9 @@ __global__ void k_rel4(const double* __restrict__ pos, const int* __restrict__ c
   int id = cell[i];
   int gx, gy, gz;
   decode_subtile(g, id, gx, gy, gz);
-  float rx = (float)__dsub_rn(pos[i], __dmul_rn((double)gx, g.side64[0]));
-  float ry = (float)__dsub_rn(pos[n + i], __dmul_rn((double)gy, g.side64[1]));
-  float rz = (float)__dsub_rn(pos[2 * n + i], __dmul_rn((double)gz, g.side64[2]));
+  float rx = (float)__fma_rn(-(double)gx, g.side64[0], pos[i]);
+  float ry = (float)__fma_rn(-(double)gy, g.side64[1], pos[n + i]);
+  float rz = (float)__fma_rn(-(double)gz, g.side64[2], pos[2 * n + i]);
   rel4[i] = make_float4(rx, ry, rz, __int_as_float(id));
 }
 
@@ -76,40 +83,63 @@ __global__ void k_compact(const int8_t* __restrict__ flag, const int* __restrict
   if (flag[i]) active_idx[act_scan[i]] = (int)i;
 }
 
-// Chunks per tile: ceil(receivers in tile / 32).
-__global__ void k_tile_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int64_t n_tiles,
-                              int nsub3, int* __restrict__ tile_chunks) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t > n_tiles) return;
-  if (t == n_tiles) {
-    tile_chunks[n_tiles] = 0;
-    return;
-  }
-  int p0 = offsets[t * nsub3], p1 = offsets[(t + 1) * nsub3];
-  int a0 = act_scan ? act_scan[p0] : p0;
-  int a1 = act_scan ? act_scan[p1] : p1;
-  tile_chunks[t] = (a1 - a0 + kChunk - 1) / kChunk;
+// Receiver chunks.  The receivers of one row of tiles (fixed tile x, y) are
+// consecutive in the sorted order; they are cut into chunks of at most 32 that
+// span at most kChunkSpan consecutive tiles along z, so that sparse tiles share
+// a warp while every chunk stays spatially compact.
+#ifndef P3M_CHUNK_SPAN
+#define P3M_CHUNK_SPAN 4
+#endif
+constexpr int kChunkSpan = P3M_CHUNK_SPAN;
+
+__device__ __forceinline__ int tile_start(const int* __restrict__ offsets, const int* __restrict__ act_scan, int nsub3,
+                                          int64_t T) {
+  int p = offsets[T * nsub3];
+  return act_scan ? act_scan[p] : p;
 }
 
-__global__ void k_write_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int64_t n_tiles,
-                               int nsub3, const int* __restrict__ tile_chunks, Chunk* __restrict__ chunks,
+// Walk row `row`; write its chunks to out (if not null); return their number.
+__device__ int walk_row(const int* __restrict__ offsets, const int* __restrict__ act_scan, int nsub3, int n_t,
+                        int64_t row, Chunk* __restrict__ out) {
+  const int64_t t0 = row * n_t, tend = t0 + n_t;
+  int s = tile_start(offsets, act_scan, nsub3, t0);
+  const int end = tile_start(offsets, act_scan, nsub3, tend);
+  int64_t T = t0;
+  int nxt = tile_start(offsets, act_scan, nsub3, T + 1);
+  int count = 0;
+  while (s < end) {
+    while (nxt <= s) {  // T: the tile holding receiver s
+      ++T;
+      nxt = tile_start(offsets, act_scan, nsub3, T + 1);
+    }
+    int64_t lim = T + kChunkSpan < tend ? T + kChunkSpan : tend;
+    int e = min(s + kChunk, tile_start(offsets, act_scan, nsub3, lim));
+    if (out) out[count] = Chunk{s, e - s};
+    ++count;
+    s = e;
+  }
+  return count;
+}
+
+__global__ void k_row_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int n_t, int nsub3,
+                             int* __restrict__ row_chunks) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rows = (int64_t)n_t * n_t;
+  if (r > rows) return;
+  row_chunks[r] = (r == rows) ? 0 : walk_row(offsets, act_scan, nsub3, n_t, r, nullptr);
+}
+
+__global__ void k_write_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int n_t, int nsub3,
+                               const int* __restrict__ row_chunks, Chunk* __restrict__ chunks,
                                int* __restrict__ n_chunks_out, int* __restrict__ n_active_out, int64_t n) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) {
-    *n_chunks_out = tile_chunks[n_tiles];
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rows = (int64_t)n_t * n_t;
+  if (r == 0) {
+    *n_chunks_out = row_chunks[rows];
     if (n_active_out) *n_active_out = act_scan ? act_scan[n] : (int)n;
   }
-  if (t >= n_tiles) return;
-  int p0 = offsets[t * nsub3], p1 = offsets[(t + 1) * nsub3];
-  int a0 = act_scan ? act_scan[p0] : p0;
-  int a1 = act_scan ? act_scan[p1] : p1;
-  int c0 = tile_chunks[t];
-  for (int k = 0; a0 + k * kChunk < a1; ++k) {
-    Chunk c;
-    c.start = a0 + k * kChunk;
-    c.count = min(kChunk, a1 - c.start);
-    chunks[c0 + k] = c;
-  }
+  if (r >= rows) return;
+  walk_row(offsets, act_scan, nsub3, n_t, r, chunks + row_chunks[r]);
 }
 
 // Masked abar for the VJP: abar_i * [i active].
@@ -198,62 +228,199 @@ struct WarpList {
   unsigned delta[kListCap];
 };
 
+// The receivers of one chunk in its frame: positions, bounding box, subtile block.
 template <class Real>
-__device__ __forceinline__ Real sq(Real v) {
-  return v * v;
+struct ChunkFrame {
+  bool valid;       // this lane holds a receiver
+  int pidx;         // its sorted particle index
+  int g0[3];        // subtile of lane 0 (frame origin)
+  Vec3<Real> pi;    // receiver position (chunk frame in FP32, absolute in FP64)
+  Vec3<Real> lo, hi;  // bounding box of the receivers
+  int elo[3], ext[3];  // candidate subtile block (offsets from g0) and its extent
+  Real org[3];      // position of g0's origin in the frame
+};
+
+template <class Real>
+__device__ __forceinline__ void load_chunk(const TraversalArgs& a, const Chunk& ch, int lane, ChunkFrame<Real>& F) {
+  const unsigned full = 0xffffffffu;
+  const Geometry& g = a.g;
+  F.valid = lane < ch.count;
+  F.pidx = 0;
+  if (F.valid) F.pidx = a.active_idx ? a.active_idx[ch.start + lane] : ch.start + lane;
+  int gi[3] = {0, 0, 0};
+  float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
+  {
+    int id = 0;
+    if constexpr (sizeof(Real) == 4) {
+      if (F.valid) ri = a.rel4[F.pidx];
+      id = __float_as_int(ri.w);
+    } else {
+      if (F.valid) id = a.cell[F.pidx];
+    }
+    if (F.valid) decode_subtile(g, id, gi[0], gi[1], gi[2]);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) F.g0[d] = __shfl_sync(full, gi[d], 0);
+  const int e[3] = {gi[0] - F.g0[0], gi[1] - F.g0[1], gi[2] - F.g0[2]};
+  if constexpr (sizeof(Real) == 4) {
+    F.pi.x = fmaf((float)e[0], g.side32[0], ri.x);
+    F.pi.y = fmaf((float)e[1], g.side32[1], ri.y);
+    F.pi.z = fmaf((float)e[2], g.side32[2], ri.z);
+  } else {
+    F.pi.x = F.valid ? a.pos[F.pidx] : 0.0;
+    F.pi.y = F.valid ? a.pos[a.n + F.pidx] : 0.0;
+    F.pi.z = F.valid ? a.pos[2 * a.n + F.pidx] : 0.0;
+  }
+  const Real big = Real(1e30);
+  F.lo.x = warp_min(F.valid ? F.pi.x : big);
+  F.lo.y = warp_min(F.valid ? F.pi.y : big);
+  F.lo.z = warp_min(F.valid ? F.pi.z : big);
+  F.hi.x = warp_max(F.valid ? F.pi.x : -big);
+  F.hi.y = warp_max(F.valid ? F.pi.y : -big);
+  F.hi.z = warp_max(F.valid ? F.pi.z : -big);
+  if (!F.valid) { F.pi.x = big; F.pi.y = big; F.pi.z = big; }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F.elo[d] = __reduce_min_sync(full, F.valid ? e[d] : 1 << 20) - g.R[d];
+    int ehi = __reduce_max_sync(full, F.valid ? e[d] : -(1 << 20)) + g.R[d];
+    F.ext[d] = ehi - F.elo[d] + 1;
+    if constexpr (sizeof(Real) == 4) F.org[d] = 0.0f;
+    else F.org[d] = (double)F.g0[d] * g.side64[d];
+  }
 }
 
-// Process the suppliers of the list entries [0, nlist) (total suppliers `total`).
+// Enumerate the subtiles of the blocky ball around the chunk's subtile block
+// (32 candidates per round, one per lane), keep those whose box gap to the
+// receivers' bounding box is below x_r and that hold particles, and append their
+// particle ranges to the warp's list; `proc(nlist, total)` consumes a full list.
+template <class Real, class Proc>
+__device__ __forceinline__ void enumerate_suppliers(const TraversalArgs& a, const ChunkFrame<Real>& F, WarpList& L,
+                                                    int lane, Proc&& proc) {
+  const unsigned full = 0xffffffffu;
+  const Geometry& g = a.g;
+  const int ncand = F.ext[0] * F.ext[1] * F.ext[2];
+  int nlist = 0, total = 0;
+  for (int cb = 0; cb < ncand; cb += kWarp) {
+    int cc = cb + lane;
+    bool take = false;
+    int start = 0, cnt = 0;
+    unsigned dpk = 0;
+    if (cc < ncand) {
+      int dz = cc % F.ext[2];
+      int t = cc / F.ext[2];
+      int dy = t % F.ext[1];
+      int dx = t / F.ext[1];
+      dx += F.elo[0]; dy += F.elo[1]; dz += F.elo[2];
+      const int dd[3] = {dx, dy, dz};
+      const Real blo[3] = {F.lo.x, F.lo.y, F.lo.z}, bhi[3] = {F.hi.x, F.hi.y, F.hi.z};
+      Real gap2 = Real(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        Real side;
+        if constexpr (sizeof(Real) == 4) side = g.side32[d]; else side = g.side64[d];
+        Real jlo = F.org[d] + Real(dd[d]) * side;
+        Real jhi = jlo + side;
+        Real gp = fmax(fmax(blo[d] - jhi, jlo - bhi[d]), Real(0));
+        gap2 += gp * gp;
+      }
+      if (gap2 < Real(a.f.margin2_f)) {
+        int gx = F.g0[0] + dx, gy = F.g0[1] + dy, gz = F.g0[2] + dz;
+        gx += gx < 0 ? g.M[0] : (gx >= g.M[0] ? -g.M[0] : 0);
+        gy += gy < 0 ? g.M[1] : (gy >= g.M[1] ? -g.M[1] : 0);
+        gz += gz < 0 ? g.M[2] : (gz >= g.M[2] ? -g.M[2] : 0);
+        int sid = encode_subtile(g, gx, gy, gz);
+        start = a.offsets[sid];
+        cnt = a.offsets[sid + 1] - start;
+        take = cnt > 0;
+        dpk = pack_delta(dx, dy, dz);
+      }
+    }
+    unsigned tm = __ballot_sync(full, take);
+    int ntake = __popc(tm);
+    if (ntake == 0) continue;
+    if (nlist + ntake > kListCap) {
+      __syncwarp();
+      proc(nlist, total);
+      __syncwarp();
+      nlist = 0;
+      total = 0;
+    }
+    int v = take ? cnt : 0;  // inclusive scan of the taken counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(full, v, o);
+      if (lane >= o) v += u;
+    }
+    int round_total = __shfl_sync(full, v, 31);
+    if (take) {
+      int slot = nlist + __popc(tm & ((1u << lane) - 1u));
+      L.start[slot] = start;
+      L.pre[slot] = total + v - cnt;
+      L.delta[slot] = dpk;
+    }
+    nlist += ntake;
+    total += round_total;
+  }
+  __syncwarp();
+  if (nlist > 0) proc(nlist, total);
+  __syncwarp();
+}
+
+// Load supplier number f of the list (lane-parallel): its position in the
+// chunk frame (FP32) or its nearest image in absolute coordinates (FP64),
+// and for the VJP its masked abar.  Returns whether it can reach the receivers'
+// bounding box.
+template <class Real, bool VJP>
+__device__ __forceinline__ bool load_supplier(const TraversalArgs& a, const WarpList& L, int nlist, int f,
+                                              const ChunkFrame<Real>& F, Vec3<Real>& pj, Vec3<Real>& aj) {
+  int lo_e = 0, hi_e = nlist - 1;  // last entry with pre <= f
+  while (lo_e < hi_e) {
+    int mid = (lo_e + hi_e + 1) >> 1;
+    if (L.pre[mid] <= f) lo_e = mid; else hi_e = mid - 1;
+  }
+  int j = L.start[lo_e] + (f - L.pre[lo_e]);
+  int dx, dy, dz;
+  unpack_delta(L.delta[lo_e], dx, dy, dz);
+  if constexpr (sizeof(Real) == 4) {
+    float4 r = a.rel4[j];
+    pj.x = fmaf((float)dx, a.g.side32[0], r.x);
+    pj.y = fmaf((float)dy, a.g.side32[1], r.y);
+    pj.z = fmaf((float)dz, a.g.side32[2], r.z);
+    if (VJP) {
+      float4 q = a.abar4[j];
+      aj.x = q.x; aj.y = q.y; aj.z = q.z;
+    }
+  } else {
+    int gx = F.g0[0] + dx, gy = F.g0[1] + dy, gz = F.g0[2] + dz;
+    double sx = gx < 0 ? -a.g.box : (gx >= a.g.M[0] ? a.g.box : 0.0);
+    double sy = gy < 0 ? -a.g.box : (gy >= a.g.M[1] ? a.g.box : 0.0);
+    double sz = gz < 0 ? -a.g.box : (gz >= a.g.M[2] ? a.g.box : 0.0);
+    pj.x = a.pos[j] + sx;
+    pj.y = a.pos[a.n + j] + sy;
+    pj.z = a.pos[2 * a.n + j] + sz;
+    if (VJP) {
+      aj.x = a.abar_d[j]; aj.y = a.abar_d[a.n + j]; aj.z = a.abar_d[2 * a.n + j];
+    }
+  }
+  Real tx = fmax(fmax(F.lo.x - pj.x, pj.x - F.hi.x), Real(0));
+  Real ty = fmax(fmax(F.lo.y - pj.y, pj.y - F.hi.y), Real(0));
+  Real tz = fmax(fmax(F.lo.z - pj.z, pj.z - F.hi.z), Real(0));
+  return (tx * tx + ty * ty + tz * tz) < Real(a.f.margin2_f);
+}
+
+// Generic path (FP64 forward, and the adjoint in both precisions): every
+// surviving supplier is broadcast with shuffles and evaluated by all lanes.
 template <class Real, bool VJP, int SOFT>
 __device__ __forceinline__ void process_list(const TraversalArgs& a, const WarpList& L, int nlist, int total, int lane,
-                                             const int g0[3], const Vec3<Real>& pi, const Vec3<Real>& lo,
-                                             const Vec3<Real>& hi, const Vec3<Real>& abar_i, Vec3<Real>& acc,
+                                             const ChunkFrame<Real>& F, const Vec3<Real>& abar_i, Vec3<Real>& acc,
                                              int& hits) {
   const unsigned full = 0xffffffffu;
   for (int b = 0; b < total; b += kWarp) {
     int f = b + lane;
-    bool have = f < total;
     Vec3<Real> pj = {Real(0), Real(0), Real(0)};
     Vec3<Real> aj = {Real(0), Real(0), Real(0)};
     bool keep = false;
-    if (have) {
-      // entry e: last entry with pre[e] <= f
-      int lo_e = 0, hi_e = nlist - 1;
-      while (lo_e < hi_e) {
-        int mid = (lo_e + hi_e + 1) >> 1;
-        if (L.pre[mid] <= f) lo_e = mid; else hi_e = mid - 1;
-      }
-      int j = L.start[lo_e] + (f - L.pre[lo_e]);
-      int dx, dy, dz;
-      unpack_delta(L.delta[lo_e], dx, dy, dz);
-      if constexpr (sizeof(Real) == 4) {
-        float4 r = a.rel4[j];
-        pj.x = fmaf((float)dx, a.g.side32[0], r.x);
-        pj.y = fmaf((float)dy, a.g.side32[1], r.y);
-        pj.z = fmaf((float)dz, a.g.side32[2], r.z);
-        if (VJP) {
-          float4 q = a.abar4[j];
-          aj.x = q.x; aj.y = q.y; aj.z = q.z;
-        }
-      } else {
-        // absolute coordinates of the image of j nearest to the chunk
-        int gx = g0[0] + dx, gy = g0[1] + dy, gz = g0[2] + dz;
-        double sx = gx < 0 ? -a.g.box : (gx >= a.g.M[0] ? a.g.box : 0.0);
-        double sy = gy < 0 ? -a.g.box : (gy >= a.g.M[1] ? a.g.box : 0.0);
-        double sz = gz < 0 ? -a.g.box : (gz >= a.g.M[2] ? a.g.box : 0.0);
-        pj.x = a.pos[j] + sx;
-        pj.y = a.pos[a.n + j] + sy;
-        pj.z = a.pos[2 * a.n + j] + sz;
-        if (VJP) {
-          aj.x = a.abar_d[j]; aj.y = a.abar_d[a.n + j]; aj.z = a.abar_d[2 * a.n + j];
-        }
-      }
-      // distance from j to the chunk's bounding box
-      Real tx = fmax(fmax(lo.x - pj.x, pj.x - hi.x), Real(0));
-      Real ty = fmax(fmax(lo.y - pj.y, pj.y - hi.y), Real(0));
-      Real tz = fmax(fmax(lo.z - pj.z, pj.z - hi.z), Real(0));
-      keep = (tx * tx + ty * ty + tz * tz) < Real(a.f.margin2_f);
-    }
+    if (f < total) keep = load_supplier<Real, VJP>(a, L, nlist, f, F, pj, aj);
     unsigned m = __ballot_sync(full, keep);
     while (m) {
       int src = __ffs(m) - 1;
@@ -261,7 +428,7 @@ __device__ __forceinline__ void process_list(const TraversalArgs& a, const WarpL
       Real xj = __shfl_sync(full, pj.x, src);
       Real yj = __shfl_sync(full, pj.y, src);
       Real zj = __shfl_sync(full, pj.z, src);
-      Real dx = pi.x - xj, dy = pi.y - yj, dz = pi.z - zj;
+      Real dx = F.pi.x - xj, dy = F.pi.y - yj, dz = F.pi.z - zj;
       Real r2 = dx * dx + dy * dy + dz * dz;
       bool hit;
       if constexpr (sizeof(Real) == 4) hit = r2 < a.f.xr2_f; else hit = r2 < a.f.xr2_d;
@@ -306,174 +473,165 @@ __device__ __forceinline__ void process_list(const TraversalArgs& a, const WarpL
   }
 }
 
+template <class Real>
+__device__ __forceinline__ void store_result(const TraversalArgs& a, const ChunkFrame<Real>& F, const Vec3<Real>& acc) {
+  if (!F.valid) return;
+  const Real s = -Real(a.f.G_m);
+  Real* o = (Real*)a.out;
+  o[F.pidx] = s * acc.x;
+  o[a.n + F.pidx] = s * acc.y;
+  o[2 * a.n + F.pidx] = s * acc.z;
+}
+
+__device__ __forceinline__ int next_chunk(const TraversalArgs& a, int lane) {
+  int c = 0;
+  if (lane == 0) c = atomicAdd(a.counter, 1);
+  return __shfl_sync(0xffffffffu, c, 0);
+}
+
 template <class Real, bool VJP, int SOFT>
 __global__ void __launch_bounds__(kForceThreads) k_traverse(TraversalArgs a) {
   __shared__ WarpList lists[kForceWarps];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   WarpList& L = lists[threadIdx.x >> 5];
-  const Geometry& g = a.g;
   const int n_chunks = *a.n_chunks;
   unsigned long long pair_total = 0;
-
   for (;;) {
-    int c = 0;
-    if (lane == 0) c = atomicAdd(a.counter, 1);
-    c = __shfl_sync(full, c, 0);
+    const int c = next_chunk(a, lane);
     if (c >= n_chunks) break;
-    const Chunk ch = a.chunks[c];
-    const bool valid = lane < ch.count;
-    int pidx = 0;
-    if (valid) pidx = a.active_idx ? a.active_idx[ch.start + lane] : ch.start + lane;
-
-    // receiver position, its subtile and the chunk frame
-    int gi[3] = {0, 0, 0};
-    Vec3<Real> pi;
-    float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
-    {
-      int id = 0;
-      if constexpr (sizeof(Real) == 4) {
-        if (valid) ri = a.rel4[pidx];
-        id = __float_as_int(ri.w);
-      } else {
-        if (valid) id = a.cell[pidx];
-      }
-      if (valid) decode_subtile(g, id, gi[0], gi[1], gi[2]);
-    }
-    int g0[3];
-    g0[0] = __shfl_sync(full, gi[0], 0);
-    g0[1] = __shfl_sync(full, gi[1], 0);
-    g0[2] = __shfl_sync(full, gi[2], 0);
-    const int e[3] = {gi[0] - g0[0], gi[1] - g0[1], gi[2] - g0[2]};
-    if constexpr (sizeof(Real) == 4) {
-      pi.x = fmaf((float)e[0], g.side32[0], ri.x);
-      pi.y = fmaf((float)e[1], g.side32[1], ri.y);
-      pi.z = fmaf((float)e[2], g.side32[2], ri.z);
-    } else {
-      pi.x = a.pos[pidx];
-      pi.y = a.pos[a.n + pidx];
-      pi.z = a.pos[2 * a.n + pidx];
-    }
-    const Real big = Real(1e30);
-    Vec3<Real> lo, hi;
-    lo.x = warp_min(valid ? pi.x : big);
-    lo.y = warp_min(valid ? pi.y : big);
-    lo.z = warp_min(valid ? pi.z : big);
-    hi.x = warp_max(valid ? pi.x : -big);
-    hi.y = warp_max(valid ? pi.y : -big);
-    hi.z = warp_max(valid ? pi.z : -big);
-    if (!valid) { pi.x = big; pi.y = big; pi.z = big; }
+    ChunkFrame<Real> F;
+    load_chunk<Real>(a, a.chunks[c], lane, F);
     Vec3<Real> abar_i = {Real(0), Real(0), Real(0)};
-    if (VJP && valid) {
+    if (VJP && F.valid) {
       if constexpr (sizeof(Real) == 4) {
-        float4 q = a.abar4[pidx];
+        float4 q = a.abar4[F.pidx];
         abar_i.x = q.x; abar_i.y = q.y; abar_i.z = q.z;
       } else {
-        abar_i.x = a.abar_d[pidx]; abar_i.y = a.abar_d[a.n + pidx]; abar_i.z = a.abar_d[2 * a.n + pidx];
+        abar_i.x = a.abar_d[F.pidx]; abar_i.y = a.abar_d[a.n + F.pidx]; abar_i.z = a.abar_d[2 * a.n + F.pidx];
       }
     }
-    int elo[3], ehi[3], ext[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      elo[d] = __reduce_min_sync(full, valid ? e[d] : 1 << 20) - g.R[d];
-      ehi[d] = __reduce_max_sync(full, valid ? e[d] : -(1 << 20)) + g.R[d];
-      ext[d] = ehi[d] - elo[d] + 1;
-    }
-    // frame origin of the subtile block (chunk frame for FP32, absolute for FP64)
-    Real org[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if constexpr (sizeof(Real) == 4) org[d] = 0.0f;
-      else org[d] = (double)g0[d] * g.side64[d];
-    }
-    const int ncand = ext[0] * ext[1] * ext[2];
     Vec3<Real> acc = {Real(0), Real(0), Real(0)};
     int hits = 0;
-    int nlist = 0, total = 0;
-    for (int cb = 0; cb < ncand; cb += kWarp) {
-      int cc = cb + lane;
-      bool take = false;
-      int start = 0, cnt = 0;
-      unsigned dpk = 0;
-      if (cc < ncand) {
-        int dz = cc % ext[2];
-        int t = cc / ext[2];
-        int dy = t % ext[1];
-        int dx = t / ext[1];
-        dx += elo[0]; dy += elo[1]; dz += elo[2];
-        Real side[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          if constexpr (sizeof(Real) == 4) side[d] = g.side32[d]; else side[d] = g.side64[d];
-        }
-        const int dd[3] = {dx, dy, dz};
-        const Real blo[3] = {lo.x, lo.y, lo.z}, bhi[3] = {hi.x, hi.y, hi.z};
-        Real gap2 = Real(0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          Real jlo = org[d] + Real(dd[d]) * side[d];
-          Real jhi = jlo + side[d];
-          Real gp = fmax(fmax(blo[d] - jhi, jlo - bhi[d]), Real(0));
-          gap2 += gp * gp;
-        }
-        if (gap2 < Real(a.f.margin2_f)) {
-          int gx = g0[0] + dx, gy = g0[1] + dy, gz = g0[2] + dz;
-          gx += gx < 0 ? g.M[0] : (gx >= g.M[0] ? -g.M[0] : 0);
-          gy += gy < 0 ? g.M[1] : (gy >= g.M[1] ? -g.M[1] : 0);
-          gz += gz < 0 ? g.M[2] : (gz >= g.M[2] ? -g.M[2] : 0);
-          int sid = encode_subtile(g, gx, gy, gz);
-          start = a.offsets[sid];
-          cnt = a.offsets[sid + 1] - start;
-          take = cnt > 0;
-          dpk = pack_delta(dx, dy, dz);
-        }
-      }
-      unsigned tm = __ballot_sync(full, take);
-      int ntake = __popc(tm);
-      if (ntake == 0) continue;
-      if (nlist + ntake > kListCap) {
-        __syncwarp();
-        process_list<Real, VJP, SOFT>(a, L, nlist, total, lane, g0, pi, lo, hi, abar_i, acc, hits);
-        __syncwarp();
-        nlist = 0;
-        total = 0;
-      }
-      // inclusive scan of the counts of the taken lanes
-      int v = take ? cnt : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(full, v, o);
-        if (lane >= o) v += u;
-      }
-      int round_total = __shfl_sync(full, v, 31);
-      if (take) {
-        int slot = nlist + __popc(tm & ((1u << lane) - 1u));
-        L.start[slot] = start;
-        L.pre[slot] = total + v - cnt;
-        L.delta[slot] = dpk;
-      }
-      nlist += ntake;
-      total += round_total;
-    }
-    __syncwarp();
-    if (nlist > 0) process_list<Real, VJP, SOFT>(a, L, nlist, total, lane, g0, pi, lo, hi, abar_i, acc, hits);
-    __syncwarp();
+    enumerate_suppliers<Real>(a, F, L, lane, [&](int nlist, int total) {
+      process_list<Real, VJP, SOFT>(a, L, nlist, total, lane, F, abar_i, acc, hits);
+    });
+    store_result<Real>(a, F, acc);
+    if (F.valid) hits -= 1;  // the receiver met itself once (r = 0)
+    pair_total += (unsigned long long)__reduce_add_sync(full, (unsigned)hits);
+  }
+  if (lane == 0 && pair_total) atomicAdd(a.pairs, pair_total);
+}
 
-    if (valid) {
-      const Real s = -Real(a.f.G_m);
-      if constexpr (sizeof(Real) == 4) {
-        float* o = (float*)a.out;
-        o[pidx] = s * acc.x;
-        o[a.n + pidx] = s * acc.y;
-        o[2 * a.n + pidx] = s * acc.z;
-      } else {
-        double* o = (double*)a.out;
-        o[pidx] = s * acc.x;
-        o[a.n + pidx] = s * acc.y;
-        o[2 * a.n + pidx] = s * acc.z;
+// ---------------------------------------------------------------------------
+// FP32 forward, packed broadcast variant: the structure of the generic kernel
+// (32 receivers per warp, every surviving supplier tested by all lanes), but
+// the survivors of a batch are staged, compacted and negated, in shared memory
+// as packed pairs, read back with broadcast loads, and two suppliers are
+// evaluated per step in f32x2 arithmetic.
+// ---------------------------------------------------------------------------
+
+constexpr int kPThreads = 128;
+constexpr int kPWarps = kPThreads / kWarp;
+
+struct PackedSmem {
+  WarpList L;
+  float4 sxy[kWarp / 2 + 1];  // (-xa, -xb, -ya, -yb)
+  float2 sz[kWarp / 2 + 1];   // (-za, -zb)
+};
+
+// 6 resident blocks of 4 warps per SM bound the kernel to ~80 registers;
+// measured best among 1, 6 and 8 on the 128^3 set.
+#ifndef P3M_GP_MINBLOCKS
+#define P3M_GP_MINBLOCKS 6
+#endif
+
+template <int SOFT>
+__global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(TraversalArgs a) {
+  __shared__ PackedSmem smem[kPWarps];
+
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  PackedSmem& S = smem[threadIdx.x >> 5];
+  const int n_chunks = *a.n_chunks;
+  const float xr2 = a.f.xr2_f;
+  unsigned long long pair_total = 0;
+  for (;;) {
+    const int c = next_chunk(a, lane);
+    if (c >= n_chunks) break;
+    ChunkFrame<float> F;
+    load_chunk<float>(a, a.chunks[c], lane, F);
+    const f2 px = pk(F.pi.x, F.pi.x), py = pk(F.pi.y, F.pi.y), pz = pk(F.pi.z, F.pi.z);
+    f2 ax = pk(0.f, 0.f), ay = pk(0.f, 0.f), az = pk(0.f, 0.f);
+    int hits = 0;
+    enumerate_suppliers<float>(a, F, S.L, lane, [&](int nlist, int total) {
+      float* sxy = (float*)S.sxy;
+      float* sz = (float*)S.sz;
+      for (int b = 0; b < total; b += kWarp) {
+        const int f = b + lane;
+        Vec3<float> pj = {0.f, 0.f, 0.f}, aj;
+        bool keep = false;
+        if (f < total) keep = load_supplier<float, false>(a, S.L, nlist, f, F, pj, aj);
+        const unsigned m = __ballot_sync(full, keep);
+        const int nsurv = __popc(m);
+        if (keep) {
+          const int k = __popc(m & ((1u << lane) - 1u));
+          const int p = k >> 1, h = k & 1;
+          sxy[4 * p + h] = -pj.x;
+          sxy[4 * p + 2 + h] = -pj.y;
+          sz[2 * p + h] = -pj.z;
+        }
+        if (lane == 0 && (nsurv & 1)) {  // pad the last pair far from every receiver
+          const int p = nsurv >> 1;
+          sxy[4 * p + 1] = 1e30f;
+          sxy[4 * p + 3] = 1e30f;
+          sz[2 * p + 1] = 1e30f;
+        }
+        __syncwarp();
+        const int npairs = (nsurv + 1) >> 1;
+        for (int p = 0; p < npairs; ++p) {
+          const float4 s = S.sxy[p];
+          const float2 z = S.sz[p];
+          const f2 dx = add2(px, pk(s.x, s.y));
+          const f2 dy = add2(py, pk(s.z, s.w));
+          const f2 dz = add2(pz, pk(z.x, z.y));
+          const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+          float q0, q1;
+          upk(r2, q0, q1);
+          const bool h0 = q0 < xr2, h1 = q1 < xr2;
+          if (__any_sync(full, h0 || h1)) {
+            hits += (int)h0 + (int)h1;
+            const bool u0 = h0 && q0 > 0.0f, u1 = h1 && q1 > 0.0f;
+            f2 B = bracket_main_f32x2<SOFT>(pk(u0 ? q0 : 1.0f, u1 ? q1 : 1.0f), a.f);
+            float b0, b1;
+            upk(B, b0, b1);
+            const bool rare0 = u0 && (q0 < a.f.rsw2_f), rare1 = u1 && (q1 < a.f.rsw2_f);
+            if (__any_sync(full, rare0 || rare1)) {
+              float Ds;
+              const float s0 = bracket_soft_f32<SOFT, false>(u0 ? q0 : 1.0f, a.f, a.sc, Ds);
+              const float s1 = bracket_soft_f32<SOFT, false>(u1 ? q1 : 1.0f, a.f, a.sc, Ds);
+              if (rare0) b0 = s0;
+              if (rare1) b1 = s1;
+            }
+            B = pk(u0 ? b0 : 0.0f, u1 ? b1 : 0.0f);
+            ax = fma2(B, dx, ax);
+            ay = fma2(B, dy, ay);
+            az = fma2(B, dz, az);
+          }
+        }
+        __syncwarp();
       }
-      hits -= 1;  // the receiver met itself once (r = 0)
-    }
+    });
+    Vec3<float> acc;
+    float l, h;
+    upk(ax, l, h);
+    acc.x = l + h;
+    upk(ay, l, h);
+    acc.y = l + h;
+    upk(az, l, h);
+    acc.z = l + h;
+    store_result<float>(a, F, acc);
+    hits = F.valid ? hits - 1 : 0;  // the receiver met itself once (r = 0)
     pair_total += (unsigned long long)__reduce_add_sync(full, (unsigned)hits);
   }
   if (lane == 0 && pair_total) atomicAdd(a.pairs, pair_total);
@@ -506,15 +664,22 @@ static SeriesConsts make_series() {
 
 template <class Real, bool VJP, int SOFT>
 static cudaError_t launch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
+  constexpr bool packed = (sizeof(Real) == 4) && !VJP;  // FP32 forward: packed broadcast kernel
   static int blocks_per_sm = 0;
   if (blocks_per_sm == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_traverse<Real, VJP, SOFT>, kForceThreads, 0);
+    if (packed)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_force_packed<SOFT>, kPThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_traverse<Real, VJP, SOFT>, kForceThreads, 0);
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
   unsigned grid = (unsigned)(ctx->num_sms * blocks_per_sm);
   const int slot = VJP ? 1 : 0;
   cudaEventRecord(ctx->kt_ev[2 * slot], ctx->stream);
-  k_traverse<Real, VJP, SOFT><<<grid, kForceThreads, 0, ctx->stream>>>(a);
+  if (packed)
+    k_force_packed<SOFT><<<grid, kPThreads, 0, ctx->stream>>>(a);
+  else
+    k_traverse<Real, VJP, SOFT><<<grid, kForceThreads, 0, ctx->stream>>>(a);
   ++ctx->launches;
   cudaEventRecord(ctx->kt_ev[2 * slot + 1], ctx->stream);
   ctx->kt_pending[slot] = true;
@@ -533,18 +698,19 @@ static cudaError_t dispatch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
 static p3m_status build_chunks(p3m_sr_ctx* ctx, const int* act_scan, Chunk* chunks, int* n_chunks_dev,
                                int* n_active_dev) {
   cudaStream_t s = ctx->stream;
-  const int64_t nt = ctx->n_tiles;
-  k_tile_chunks<<<blocks_for(nt + 1, 256), 256, 0, s>>>(ctx->offsets, act_scan, nt, ctx->geo.nsub3,
+  const int n_t = ctx->geo.n_t;
+  const int64_t rows = (int64_t)n_t * n_t;
+  k_row_chunks<<<blocks_for(rows + 1, 128), 128, 0, s>>>(ctx->offsets, act_scan, n_t, ctx->geo.nsub3,
                                                          ctx->tile_chunks);
   ++ctx->launches;
-  p3m_status st = cuda_check(ctx, cudaGetLastError(), "tile chunk kernel");
+  p3m_status st = cuda_check(ctx, cudaGetLastError(), "row chunk kernel");
   if (st != P3M_OK) return st;
-  st = cuda_check(ctx, scan_exclusive_i32(ctx->tile_chunks, ctx->tile_chunks, nt + 1, ctx->scan_scratch, s, &ctx->launches),
-                  "chunk scan");
+  st = cuda_check(ctx, scan_exclusive_i32(ctx->tile_chunks, ctx->tile_chunks, rows + 1, ctx->scan_scratch, s,
+                                          &ctx->launches), "chunk scan");
   if (st != P3M_OK) return st;
-  k_write_chunks<<<blocks_for(nt > 0 ? nt : 1, 256), 256, 0, s>>>(ctx->offsets, act_scan, nt, ctx->geo.nsub3,
-                                                                   ctx->tile_chunks, chunks, n_chunks_dev,
-                                                                   n_active_dev, ctx->n);
+  k_write_chunks<<<blocks_for(rows, 128), 128, 0, s>>>(ctx->offsets, act_scan, n_t, ctx->geo.nsub3,
+                                                        ctx->tile_chunks, chunks, n_chunks_dev, n_active_dev,
+                                                        ctx->n);
   ++ctx->launches;
   return cuda_check(ctx, cudaGetLastError(), "write chunks kernel");
 }

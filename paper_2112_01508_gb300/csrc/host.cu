@@ -150,7 +150,7 @@ using namespace p3m;
 // Parameter validation and constants.
 // ---------------------------------------------------------------------------
 
-static p3m_status validate(p3m_sr_ctx* ctx, const p3m_sr_params& p) {
+p3m_status validate_params(p3m_sr_ctx* ctx, const p3m_sr_params& p) {
   if (p.n < 0 || p.n > 0x7fffffffLL - 64) return fail(ctx, P3M_ERR_INVALID, "n must be in [0, 2^31 - 64)");
   if (!(p.box > 0.0) || !std::isfinite(p.box)) return fail(ctx, P3M_ERR_INVALID, "box must be positive");
   if (!(p.x_s > 0.0) || !std::isfinite(p.x_s)) return fail(ctx, P3M_ERR_INVALID, "x_s must be positive");
@@ -170,7 +170,7 @@ static p3m_status validate(p3m_sr_ctx* ctx, const p3m_sr_params& p) {
   return P3M_OK;
 }
 
-static void setup_geometry(p3m_sr_ctx* ctx) {
+void setup_geometry(p3m_sr_ctx* ctx) {
   const p3m_sr_params& p = ctx->prm;
   Geometry& g = ctx->geo;
   g.n_t = (int)std::floor(p.box / p.x_r);
@@ -190,7 +190,7 @@ static void setup_geometry(p3m_sr_ctx* ctx) {
   ctx->n_tiles = (int64_t)g.n_t * g.n_t * g.n_t;
 }
 
-static void setup_force_consts(p3m_sr_ctx* ctx) {
+void setup_force_consts(p3m_sr_ctx* ctx) {
   const p3m_sr_params& p = ctx->prm;
   ForceConsts& f = ctx->fc;
   const double pi = 3.14159265358979323846;
@@ -240,7 +240,7 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
   if (!params) return P3M_ERR_INVALID;
   p3m_sr_ctx* ctx = new (std::nothrow) p3m_sr_ctx();
   if (!ctx) return P3M_ERR_OOM;
-  p3m_status st = validate(ctx, *params);
+  p3m_status st = validate_params(ctx, *params);
   if (st != P3M_OK) {
     delete ctx;
     return st;
@@ -259,17 +259,17 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
 
   const int64_t n = ctx->n;
   const int64_t S = ctx->geo.S;
-  // radix passes over ceil(log2(S)) key bits, at most 8 bits each
+  // radix passes over ceil(log2(S)) key bits, at most 10 bits each
   int key_bits = 1;
   while (key_bits < 31 && ((int64_t)1 << key_bits) < S) ++key_bits;
-  ctx->radix_passes = (key_bits + 7) / 8;
+  ctx->radix_passes = (key_bits + 9) / 10;
   for (int k = 0, left = key_bits; k < ctx->radix_passes; ++k) {
     int b = (left + (ctx->radix_passes - k) - 1) / (ctx->radix_passes - k);
     ctx->radix_bits[k] = b;
     left -= b;
   }
   int64_t radix_blocks = (n + 4095) / 4096;
-  ctx->hist_ints = 256 * (radix_blocks > 0 ? radix_blocks : 1);
+  ctx->hist_ints = 1024 * (radix_blocks > 0 ? radix_blocks : 1);
   int64_t scan_n = std::max<int64_t>(std::max<int64_t>(S + 1, n + 1), std::max<int64_t>(ctx->hist_ints, ctx->n_tiles + 1));
   ctx->scan_scratch_ints = scan_scratch_ints(scan_n);
   ctx->max_chunks = std::min<int64_t>(n, ctx->n_tiles) + (n + kChunk - 1) / kChunk + 1;

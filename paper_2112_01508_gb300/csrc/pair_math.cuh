@@ -44,6 +44,35 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// Packed pairs of floats (sm_100+ f32x2 arithmetic): one instruction issues
+// two FP32 lanes' worth of work, halving the issue slots of the FP32 chain.
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk(f2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+
 // ---------------------------------------------------------------- FP32 ----
 
 // Main branch.  Returns B; with VJP also D = B'(r)/r.
@@ -72,6 +101,40 @@ __device__ __forceinline__ float bracket_main_f32(float r2, const ForceConsts& f
     float rinv3 = rinv2 * rinv;
     if (VJP) D += 3.0f * (rinv3 * rinv2 - p3 * p * p);
     B += p3 - rinv3;
+  }
+  return B;
+}
+
+// Main branch for two pairs at once (forward only): the FP32 chain of
+// bracket_main_f32 in packed f32x2 form; the SFU operations stay scalar.
+template <int SOFT>
+__device__ __forceinline__ f2 bracket_main_f32x2(f2 r2, const ForceConsts& f) {
+  float a, b;
+  upk(r2, a, b);
+  const f2 rinv = pk(rsqrt_approx(a), rsqrt_approx(b));
+  const f2 r = mul2(r2, rinv);
+  float ea, eb;
+  upk(mul2(r2, pk(f.ce_f, f.ce_f)), ea, eb);
+  const f2 e = pk(ex2_approx(ea), ex2_approx(eb));
+  float da, db;
+  upk(fma2(r, pk(f.kc_f, f.kc_f), pk(1.0f, 1.0f)), da, db);
+  const f2 t = pk(rcp_approx(da), rcp_approx(db));
+  f2 q = fma2(pk(f.c_f[5], f.c_f[5]), t, pk(f.c_f[4], f.c_f[4]));
+  q = fma2(q, t, pk(f.c_f[3], f.c_f[3]));
+  q = fma2(q, t, pk(f.c_f[2], f.c_f[2]));
+  q = fma2(q, t, pk(f.c_f[1], f.c_f[1]));
+  q = fma2(q, t, pk(f.c_f[0], f.c_f[0]));
+  const f2 ex = mul2(q, t);
+  const f2 rinv2 = mul2(rinv, rinv);
+  const f2 er2 = mul2(e, rinv2);
+  f2 B = mul2(er2, fma2(ex, rinv, pk(f.k2_f, f.k2_f)));
+  if (SOFT == P3M_SOFT_PLUMMER) {
+    float pa, pb;
+    upk(add2(r2, pk(f.eps2_f, f.eps2_f)), pa, pb);
+    const f2 p = pk(rsqrt_approx(pa), rsqrt_approx(pb));
+    const f2 p3 = mul2(mul2(p, p), p);
+    const f2 rinv3 = mul2(rinv2, rinv);
+    B = add2(B, fma2(rinv3, pk(-1.0f, -1.0f), p3));
   }
   return B;
 }

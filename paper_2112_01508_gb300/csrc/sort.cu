@@ -8,6 +8,8 @@
 // comes from a stable LSD radix sort of the subtile ids (8-bit digits at
 // most, warp-level ranking with match.any so that equal ids keep their input
 // order), after which positions and any carried arrays are gathered.
+#include <string>
+
 #include "ctx.cuh"
 
 namespace p3m {
@@ -16,32 +18,41 @@ constexpr int kRadixThreads = 256;
 constexpr int kRadixWarps = kRadixThreads / kWarp;
 constexpr int kRadixSteps = 16;                           // items per lane
 constexpr int kRadixTile = kRadixThreads * kRadixSteps;   // 4096 items per block
+static_assert(kRadixThreads == kRadixThreadsPublic && kRadixTile == kRadixTilePublic, "radix tiling");
 
 __global__ void k_bin(const double* __restrict__ pos, int64_t n, Geometry g, int* __restrict__ keys,
                       int* __restrict__ vals, int* __restrict__ counts, int* __restrict__ err) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int gc[3];
-  bool bad = false;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < n;  // every lane stays for the warp-wide match below
+  int id = 0;
+  if (valid) {
+    int gc[3];
+    bool bad = false;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    double v = pos[d * n + i];
-    bool ok = (v >= 0.0) && (v < g.box);  // false for NaN
-    bad |= !ok;
-    double p = __dmul_rn(ok ? v : 0.0, g.scale64[d]);
-    int q = (int)p;  // p >= 0: truncation is floor
-    gc[d] = q < g.M[d] - 1 ? q : g.M[d] - 1;
+    for (int d = 0; d < 3; ++d) {
+      double v = pos[d * n + i];
+      bool ok = (v >= 0.0) && (v < g.box);  // false for NaN
+      bad |= !ok;
+      double p = __dmul_rn(ok ? v : 0.0, g.scale64[d]);
+      int q = (int)p;  // p >= 0: truncation is floor
+      gc[d] = q < g.M[d] - 1 ? q : g.M[d] - 1;
+    }
+    if (bad) atomicOr(err, kErrPosition);
+    id = encode_subtile(g, gc[0], gc[1], gc[2]);
+    keys[i] = id;
+    vals[i] = (int)i;
   }
-  if (bad) atomicOr(err, kErrPosition);
-  int id = encode_subtile(g, gc[0], gc[1], gc[2]);
-  keys[i] = id;
-  vals[i] = (int)i;
-  atomicAdd(&counts[id], 1);
+  // one atomic per distinct subtile in the warp (sorted input repeats ids)
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, valid ? id : -1 - lane);
+  if (valid && lane == __ffs(peers) - 1) atomicAdd(&counts[id], __popc(peers));
 }
+
+constexpr int kMaxRadix = 1024;  // digits of at most 10 bits
 
 __global__ void k_radix_hist(const int* __restrict__ keys, int64_t n, int shift, int bits,
                              int* __restrict__ hist, int nblocks) {
-  __shared__ int cnt[256];
+  __shared__ int cnt[kMaxRadix];
   const int radix = 1 << bits;
   for (int d = threadIdx.x; d < radix; d += blockDim.x) cnt[d] = 0;
   __syncthreads();
@@ -61,7 +72,7 @@ __global__ void k_radix_hist(const int* __restrict__ keys, int64_t n, int shift,
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
     const int* __restrict__ keys_in, const int* __restrict__ vals_in, int* __restrict__ keys_out,
     int* __restrict__ vals_out, int64_t n, int shift, int bits, const int* __restrict__ hist, int nblocks) {
-  __shared__ int wcnt[kRadixWarps][256];
+  __shared__ int wcnt[kRadixWarps][kMaxRadix];
   const int radix = 1 << bits;
   const int mask = radix - 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -130,6 +141,19 @@ __global__ void k_gather_words(const T* __restrict__ src, const int* __restrict_
 }
 
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// dst[r n + k] = src[r n + perm[k]] (to sorted order) or dst[r n + perm[k]] = src[r n + k] (back).
+template <class T>
+__global__ void k_permute_rows(const T* __restrict__ src, T* __restrict__ dst, const int* __restrict__ perm, int64_t n,
+                               int rows, int to_sorted) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int64_t j = perm[k];
+  for (int r = 0; r < rows; ++r) {
+    if (to_sorted) dst[(int64_t)r * n + k] = src[(int64_t)r * n + j];
+    else dst[(int64_t)r * n + j] = src[(int64_t)r * n + k];
+  }
+}
 
 static p3m_status gather_carry(p3m_sr_ctx* ctx, void* arr, int bytes) {
   const int64_t n = ctx->n;
@@ -229,4 +253,34 @@ extern "C" p3m_status p3m_sr_sort(p3m_sr_ctx* ctx, double* pos, void* const* car
   report_latched(ctx);
   ctx->sorted = true;
   return P3M_OK;
+}
+
+static p3m_status permute_rows(p3m_sr_ctx* ctx, const void* src, void* dst, int elem_bytes, int rows, int to_sorted,
+                               const char* name) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (!ctx->sorted && !ctx->perm) return fail(ctx, P3M_ERR_STATE, std::string(name) + ": call p3m_sr_sort first");
+  if (!ctx->perm) return fail(ctx, P3M_ERR_STATE, std::string(name) + ": call p3m_sr_sort first");
+  if (rows < 1 || (elem_bytes != 1 && elem_bytes != 2 && elem_bytes != 4 && elem_bytes != 8))
+    return fail(ctx, P3M_ERR_INVALID, std::string(name) + ": elem_bytes must be 1, 2, 4 or 8 and rows >= 1");
+  const int64_t n = ctx->n;
+  if (n == 0) return P3M_OK;
+  if (!src || !dst || src == dst) return fail(ctx, P3M_ERR_INVALID, std::string(name) + ": need distinct non-null arrays");
+  const unsigned b = blocks_for(n, 256);
+  cudaStream_t s = ctx->stream;
+  switch (elem_bytes) {
+    case 1: k_permute_rows<uint8_t><<<b, 256, 0, s>>>((const uint8_t*)src, (uint8_t*)dst, ctx->perm, n, rows, to_sorted); break;
+    case 2: k_permute_rows<uint16_t><<<b, 256, 0, s>>>((const uint16_t*)src, (uint16_t*)dst, ctx->perm, n, rows, to_sorted); break;
+    case 4: k_permute_rows<uint32_t><<<b, 256, 0, s>>>((const uint32_t*)src, (uint32_t*)dst, ctx->perm, n, rows, to_sorted); break;
+    default: k_permute_rows<uint64_t><<<b, 256, 0, s>>>((const uint64_t*)src, (uint64_t*)dst, ctx->perm, n, rows, to_sorted); break;
+  }
+  ++ctx->launches;
+  return cuda_check(ctx, cudaGetLastError(), name);
+}
+
+extern "C" p3m_status p3m_sr_permute(p3m_sr_ctx* ctx, const void* src, void* dst, int elem_bytes, int rows) {
+  return permute_rows(ctx, src, dst, elem_bytes, rows, 1, "permute");
+}
+
+extern "C" p3m_status p3m_sr_unpermute(p3m_sr_ctx* ctx, const void* src, void* dst, int elem_bytes, int rows) {
+  return permute_rows(ctx, src, dst, elem_bytes, rows, 0, "unpermute");
 }

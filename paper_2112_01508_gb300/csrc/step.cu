@@ -23,12 +23,14 @@ __global__ void k_rungs(const A* __restrict__ acc, int64_t n, double qq, int n_r
   int l = 0;
   if (isnan(s) || isinf(s)) {
     atomicOr(err, kErrNonfiniteAcc);
-  } else {
-    double p = 1.0;
-    while (l < n_rung - 1 && s > p) {
-      p *= 16.0;
-      ++l;
-    }
+  } else if (s > 1.0) {
+    // smallest k with s <= 2^k from the exponent bits (s = m 2^e, m in [1, 2)):
+    // k = e if s is a power of two, else e + 1; then l = ceil(k / 4)
+    long long b = __double_as_longlong(s);
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    int k = e + (((b & 0xfffffffffffffLL) != 0) ? 1 : 0);
+    l = (k + 3) >> 2;
+    if (l > n_rung - 1) l = n_rung - 1;
   }
   rung[i] = (int8_t)l;
 }
@@ -63,8 +65,10 @@ __global__ void k_drift(double* __restrict__ pos, const M* __restrict__ mom, int
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     double v = __dadd_rn(pos[d * n + i], __dmul_rn((double)mom[d * n + i], factor));
-    v = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
-    if (v >= box || v < 0.0) v = 0.0;
+    if (v < 0.0 || v >= box) {  // v - L floor(v / L); floor is 0 inside the box
+      v = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
+      if (v >= box || v < 0.0) v = 0.0;
+    }
     pos[d * n + i] = v;
   }
 }

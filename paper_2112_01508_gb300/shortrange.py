@@ -178,6 +178,25 @@ class ShortRange:
         self._raise(nat.p3m_sr_vjp(self._ctx, pos.data_ptr(), prec, acc_bar.data_ptr(), out.data_ptr()))
         return out
 
+    def permute(self, src: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Caller order -> order of the last sort (last dimension indexes particles)."""
+        return self._perm(src, out, nat.p3m_sr_permute)
+
+    def unpermute(self, src: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Order of the last sort -> caller order."""
+        return self._perm(src, out, nat.p3m_sr_unpermute)
+
+    def _perm(self, src, out, fn):
+        _check(src, "src", device=self.device)
+        if src.shape[-1] != self.n:
+            raise ValueError("last dimension must be n")
+        if out is None:
+            out = torch.empty_like(src)
+        _check(out, "out", src.dtype, tuple(src.shape), self.device)
+        rows = src.numel() // max(self.n, 1)
+        self._raise(fn(self._ctx, src.data_ptr(), out.data_ptr(), src.element_size(), rows))
+        return out
+
     def sync(self):
         self._raise(nat.p3m_sr_sync(self._ctx))
 
