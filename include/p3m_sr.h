@@ -223,6 +223,37 @@ p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom, int mom_p
 p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precision, const void* acc_bar,
                       void* pos_bar_out);
 
+/*
+ * Allocation-free FP32 short-range accelerations for a small particle set.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory: code running inside a memory pool or arena
+ * owned by a host application, a plugin that is handed only its input and
+ * output buffers, or a pipeline that forbids cudaMalloc after start-up.  It
+ * needs no context and calls no cudaMalloc, cudaFree or other allocating
+ * routine.  It sorts the particles into tiles and subtiles, builds the
+ * receiver chunks and evaluates the FP32 forces with the same kernels as
+ * p3m_sr_sort + p3m_sr_build_pairs + p3m_sr_forces (all particles active), but
+ * keeps every intermediate array in one fixed-size device array inside the
+ * library (about 6 MB, held by every GPU that loads the library until the
+ * process exits).
+ *   params      as for p3m_sr_create; n <= 65536, at most 2^18 subtiles and
+ *               2^14 rows of tiles, x_r <= 4.6 x_s.  Larger inputs return
+ *               P3M_ERR_INVALID.
+ *   cuda_stream cudaStream_t; all work is enqueued on it (nothing is waited for).
+ *   pos         3 x n float64 SoA, device, any order, each coordinate in
+ *               [0, L); it is not modified.  Positions outside the box are
+ *               clamped into it without an error report.
+ *   acc_out     3 x n float, device: accelerations in the order of pos.
+ * The first call on a device looks up the device address of the internal array
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  Every call uses the same internal array: calls whose GPU
+ * work overlaps (other streams, other host threads) race and must be
+ * serialised by the caller.
+ */
+p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* cuda_stream, const double* pos,
+                                 float* acc_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ SOFTENING = {"none": 0, "plummer": 1, "bspline": 2}
 EXPORTS = (
     "p3m_sr_create", "p3m_sr_destroy", "p3m_sr_last_error", "p3m_sr_sync", "p3m_sr_stats", "p3m_sr_sort",
     "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
-    "p3m_sr_permute", "p3m_sr_unpermute",
+    "p3m_sr_permute", "p3m_sr_unpermute", "p3m_sr_forces_noalloc",
 )
 
 
@@ -119,6 +119,8 @@ def load() -> ctypes.CDLL:
         L.p3m_sr_permute.restype = i
         L.p3m_sr_unpermute.argtypes = [p, p, p, i, i]
         L.p3m_sr_unpermute.restype = i
+        L.p3m_sr_forces_noalloc.argtypes = [ctypes.POINTER(P3MParams), p, p, p]
+        L.p3m_sr_forces_noalloc.restype = i
         _lib = L
         return L
 

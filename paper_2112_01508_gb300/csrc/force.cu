@@ -29,6 +29,7 @@
 // strongly varying cost of clustered regions.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "ctx.cuh"
 #include "erfcx_fit.h"
@@ -851,5 +852,183 @@ extern "C" p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precisi
   cudaError_t e = (precision == 32) ? dispatch_traverse<float, true>(ctx, a) : dispatch_traverse<double, true>(ctx, a);
   if ((st = cuda_check(ctx, e, "vjp kernel")) != P3M_OK) return st;
   report_latched(ctx);
+  return P3M_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.
+//
+// Some callers cannot allocate device memory at all: code that runs under a
+// memory pool or arena owned by a host application, a plugin that is handed
+// only its input and output buffers, or a pipeline that forbids cudaMalloc
+// after start-up.  p3m_sr_forces_noalloc serves them: it sorts a small
+// particle set, builds its receiver chunks and evaluates the FP32 forces with
+// the same kernels as the context-based path, but every intermediate array
+// lives in one file-scope device array of fixed size.  That array belongs to
+// every GPU that loads the library, for as long as the process lives.
+// ---------------------------------------------------------------------------
+
+namespace p3m {
+
+constexpr int64_t kNoallocMaxN = 1 << 16;         // particles
+constexpr int64_t kNoallocMaxSubtiles = 1 << 18;  // subtiles (n_t n_sub)^3
+constexpr int64_t kNoallocMaxRows = 1 << 14;      // tile rows n_t^2
+constexpr int64_t kNoallocRadixBlocks = (kNoallocMaxN + kRadixTilePublic - 1) / kRadixTilePublic;
+constexpr int64_t kNoallocMaxChunks = kNoallocMaxN + kNoallocMaxN / kChunk + 1;
+
+constexpr int64_t noalloc_align(int64_t b) { return (b + 255) / 256 * 256; }
+
+// Byte layout of the scratch array (each part 256-byte aligned).
+struct NoallocLayout {
+  static constexpr int64_t keys0 = 0;
+  static constexpr int64_t keys1 = keys0 + noalloc_align(4 * kNoallocMaxN);
+  static constexpr int64_t vals0 = keys1 + noalloc_align(4 * kNoallocMaxN);
+  static constexpr int64_t vals1 = vals0 + noalloc_align(4 * kNoallocMaxN);
+  static constexpr int64_t offsets = vals1 + noalloc_align(4 * kNoallocMaxN);
+  static constexpr int64_t hist = offsets + noalloc_align(4 * (kNoallocMaxSubtiles + 1));
+  static constexpr int64_t scan = hist + noalloc_align(4 * 1024 * kNoallocRadixBlocks);
+  static constexpr int64_t pos = scan + noalloc_align(4 * 4096);
+  static constexpr int64_t rel4 = pos + noalloc_align(8 * 3 * kNoallocMaxN);
+  static constexpr int64_t rows = rel4 + noalloc_align(16 * kNoallocMaxN);
+  static constexpr int64_t chunks = rows + noalloc_align(4 * (kNoallocMaxRows + 1));
+  static constexpr int64_t acc = chunks + noalloc_align(8 * kNoallocMaxChunks);
+  static constexpr int64_t small = acc + noalloc_align(4 * 3 * kNoallocMaxN);
+  static constexpr int64_t total = small + noalloc_align(64);
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NoallocLayout::total];
+
+constexpr int kNoallocMaxDevices = 64;
+static void* g_noalloc_addr[kNoallocMaxDevices];
+static std::mutex g_noalloc_mutex;
+
+// acc_out[d][perm[k]] = acc[d][k]
+__global__ void k_noalloc_unsort(const float* __restrict__ acc, const int* __restrict__ perm, int64_t n,
+                                 float* __restrict__ out) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int64_t j = perm[k];
+  out[j] = acc[k];
+  out[n + j] = acc[n + k];
+  out[2 * n + j] = acc[2 * n + k];
+}
+
+}  // namespace p3m
+
+extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* cuda_stream, const double* pos,
+                                            float* acc_out) {
+  if (!params) return P3M_ERR_INVALID;
+  p3m_sr_ctx c;  // host-side bookkeeping only: no device memory, no events
+  p3m_status st = validate_params(&c, *params);
+  if (st != P3M_OK) return st;
+  const int64_t n = params->n;
+  if (n > kNoallocMaxN) return P3M_ERR_INVALID;
+  c.prm = *params;
+  c.n = n;
+  setup_geometry(&c);
+  setup_force_consts(&c);
+  const Geometry& g = c.geo;
+  if (g.S > kNoallocMaxSubtiles || (int64_t)g.n_t * g.n_t > kNoallocMaxRows) return P3M_ERR_INVALID;
+  if (params->x_r > 2.0 * P3M_ERFCX_UMAX * params->x_s) return P3M_ERR_INVALID;
+  if (n == 0) return P3M_OK;
+  if (!pos || !acc_out) return P3M_ERR_INVALID;
+
+  // once per device: the device address of the scratch array
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return P3M_ERR_CUDA;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return P3M_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = p;
+    }
+    base = (unsigned char*)g_noalloc_addr[dev];
+  }
+  using Lay = NoallocLayout;
+  int* keys[2] = {(int*)(base + Lay::keys0), (int*)(base + Lay::keys1)};
+  int* vals[2] = {(int*)(base + Lay::vals0), (int*)(base + Lay::vals1)};
+  int* offsets = (int*)(base + Lay::offsets);
+  int* hist = (int*)(base + Lay::hist);
+  int* scan = (int*)(base + Lay::scan);
+  double* spos = (double*)(base + Lay::pos);
+  float4* rel4 = (float4*)(base + Lay::rel4);
+  int* rows = (int*)(base + Lay::rows);
+  Chunk* chunks = (Chunk*)(base + Lay::chunks);
+  float* acc = (float*)(base + Lay::acc);
+  int* small = (int*)(base + Lay::small);  // [0] n_chunks, [1] counter, [2] error bits, [4..5] pair count
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int64_t launches = 0;
+  auto ok = [&](cudaError_t e) { return e == cudaSuccess; };
+
+  // bin + subtile offsets (histogram, exclusive scan)
+  if (!ok(cudaMemsetAsync(offsets, 0, sizeof(int) * (g.S + 1), s))) return P3M_ERR_CUDA;
+  if (!ok(cudaMemsetAsync(small, 0, 64, s))) return P3M_ERR_CUDA;
+  k_bin<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, g, keys[0], vals[0], offsets, small + 2);
+  if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
+  if (!ok(scan_exclusive_i32(offsets, offsets, g.S + 1, scan, s, &launches))) return P3M_ERR_CUDA;
+  // stable LSD radix sort of the subtile ids
+  int key_bits = 1;
+  while (key_bits < 31 && ((int64_t)1 << key_bits) < g.S) ++key_bits;
+  const int passes = (key_bits + 9) / 10;
+  const int nblocks = (int)((n + kRadixTilePublic - 1) / kRadixTilePublic);
+  int cur = 0, shift = 0;
+  for (int p = 0, left = key_bits; p < passes; ++p) {
+    const int bits = (left + (passes - p) - 1) / (passes - p);
+    left -= bits;
+    k_radix_hist<<<nblocks, kRadixThreadsPublic, 0, s>>>(keys[cur], n, shift, bits, hist, nblocks);
+    if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
+    if (!ok(scan_exclusive_i32(hist, hist, (int64_t)nblocks << bits, scan, s, &launches))) return P3M_ERR_CUDA;
+    k_radix_scatter<<<nblocks, kRadixThreadsPublic, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n,
+                                                            shift, bits, hist, nblocks);
+    if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
+    cur ^= 1;
+    shift += bits;
+  }
+  const int* cell = keys[cur];
+  const int* perm = vals[cur];
+  // sorted positions and their FP32 subtile-relative records
+  k_gather_pos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, perm, n, spos);
+  k_rel4<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(spos, cell, n, g, rel4);
+  // receiver chunks (all particles active)
+  const int64_t nrows = (int64_t)g.n_t * g.n_t;
+  k_row_chunks<<<(unsigned)((nrows + 1 + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows);
+  if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
+  if (!ok(scan_exclusive_i32(rows, rows, nrows + 1, scan, s, &launches))) return P3M_ERR_CUDA;
+  k_write_chunks<<<(unsigned)((nrows + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows, chunks,
+                                                                 small + 0, nullptr, n);
+  if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
+  // pair forces in the sorted order, then back to the caller's order
+  static SeriesConsts series = make_series();
+  TraversalArgs a{};
+  a.g = g;
+  a.f = c.fc;
+  a.sc = series;
+  a.pos = spos;
+  a.rel4 = rel4;
+  a.offsets = offsets;
+  a.cell = cell;
+  a.chunks = chunks;
+  a.n_chunks = small + 0;
+  a.counter = small + 1;
+  a.active_idx = nullptr;
+  a.n = n;
+  a.out = acc;
+  a.pairs = (unsigned long long*)(small + 4);
+  int num_sms = 0;
+  cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)(num_sms > 0 ? num_sms : 1) * 4;
+  switch (params->softening) {
+    case P3M_SOFT_NONE: k_force_packed<P3M_SOFT_NONE><<<grid, kPThreads, 0, s>>>(a); break;
+    case P3M_SOFT_PLUMMER: k_force_packed<P3M_SOFT_PLUMMER><<<grid, kPThreads, 0, s>>>(a); break;
+    default: k_force_packed<P3M_SOFT_BSPLINE><<<grid, kPThreads, 0, s>>>(a); break;
+  }
+  if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
+  k_noalloc_unsort<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, perm, n, acc_out);
+  if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   return P3M_OK;
 }
