@@ -134,24 +134,24 @@ def dist_setup():
     return world, rank, local
 
 
-def max_over_ranks(value: float, world: int) -> float:
+def _reduce(value: float, world: int, op_name: str) -> float:
+    """All-reduce one scalar over the ranks (NCCL on GPUs, gloo on CPU)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=getattr(dist.ReduceOp, op_name))
     return float(t.item())
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    return _reduce(value, world, "MAX")
 
 
 def sum_over_ranks(value: float, world: int) -> float:
-    if world == 1:
-        return value
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(value, world, "SUM")
 
 
 def barrier(world: int):
@@ -278,7 +278,7 @@ def run_ours(args):
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / OPS_PER_PAIR
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
                 "frac": achieved / peak, "traffic": traffic_from_profiles(),
-                "kernel": "k_traverse<float, fwd, bspline>", "kernel_ms": kern_avg_ms,
+                "kernel": "k_force_packed<bspline> (FP32 forward)", "kernel_ms": kern_avg_ms,
                 "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz / "
                               f"{OPS_PER_PAIR} FP32 ops per pair"}
 

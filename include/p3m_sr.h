@@ -238,7 +238,7 @@ p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precision, const v
  * library (about 6 MB, held by every GPU that loads the library until the
  * process exits).
  *   params      as for p3m_sr_create; n <= 65536, at most 2^18 subtiles and
- *               2^14 rows of tiles, x_r <= 4.6 x_s.  Larger inputs return
+ *               2^14 chunk segments (n_t^2 ceil(n_t/4)), x_r <= 4.6 x_s.  Larger inputs return
  *               P3M_ERR_INVALID.
  *   cuda_stream cudaStream_t; all work is enqueued on it (nothing is waited for).
  *   pos         3 x n float64 SoA, device, any order, each coordinate in

@@ -85,9 +85,10 @@ __global__ void k_compact(const int8_t* __restrict__ flag, const int* __restrict
 }
 
 // Receiver chunks.  The receivers of one row of tiles (fixed tile x, y) are
-// consecutive in the sorted order; they are cut into chunks of at most 32 that
-// span at most kChunkSpan consecutive tiles along z, so that sparse tiles share
-// a warp while every chunk stays spatially compact.
+// consecutive in the sorted order.  Each row is cut into segments of
+// kChunkSpan consecutive tiles along z, and the receivers of a segment into
+// ceil(count / 32) chunks, so that sparse tiles share a warp while every chunk
+// stays spatially compact.  One thread per segment: no sequential walk.
 #ifndef P3M_CHUNK_SPAN
 #define P3M_CHUNK_SPAN 4
 #endif
@@ -99,48 +100,49 @@ __device__ __forceinline__ int tile_start(const int* __restrict__ offsets, const
   return act_scan ? act_scan[p] : p;
 }
 
-// Walk row `row`; write its chunks to out (if not null); return their number.
-__device__ int walk_row(const int* __restrict__ offsets, const int* __restrict__ act_scan, int nsub3, int n_t,
-                        int64_t row, Chunk* __restrict__ out) {
-  const int64_t t0 = row * n_t, tend = t0 + n_t;
-  int s = tile_start(offsets, act_scan, nsub3, t0);
-  const int end = tile_start(offsets, act_scan, nsub3, tend);
-  int64_t T = t0;
-  int nxt = tile_start(offsets, act_scan, nsub3, T + 1);
-  int count = 0;
-  while (s < end) {
-    while (nxt <= s) {  // T: the tile holding receiver s
-      ++T;
-      nxt = tile_start(offsets, act_scan, nsub3, T + 1);
-    }
-    int64_t lim = T + kChunkSpan < tend ? T + kChunkSpan : tend;
-    int e = min(s + kChunk, tile_start(offsets, act_scan, nsub3, lim));
-    if (out) out[count] = Chunk{s, e - s};
-    ++count;
-    s = e;
-  }
-  return count;
+// Receiver range [a0, a1) of segment `seg` (row-major over rows, then segments).
+__device__ __forceinline__ void segment_range(const int* __restrict__ offsets, const int* __restrict__ act_scan,
+                                              int nsub3, int n_t, int64_t seg, int& a0, int& a1) {
+  const int nseg = (n_t + kChunkSpan - 1) / kChunkSpan;
+  const int64_t row = seg / nseg;
+  const int k = (int)(seg - row * nseg);
+  const int64_t t0 = row * n_t + (int64_t)k * kChunkSpan;
+  const int64_t t1 = row * n_t + min(n_t, (k + 1) * kChunkSpan);
+  a0 = tile_start(offsets, act_scan, nsub3, t0);
+  a1 = tile_start(offsets, act_scan, nsub3, t1);
 }
 
 __global__ void k_row_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int n_t, int nsub3,
-                             int* __restrict__ row_chunks) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t rows = (int64_t)n_t * n_t;
-  if (r > rows) return;
-  row_chunks[r] = (r == rows) ? 0 : walk_row(offsets, act_scan, nsub3, n_t, r, nullptr);
+                             int* __restrict__ seg_chunks) {
+  const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nsegs = (int64_t)n_t * n_t * ((n_t + kChunkSpan - 1) / kChunkSpan);
+  if (seg > nsegs) return;
+  if (seg == nsegs) {
+    seg_chunks[nsegs] = 0;
+    return;
+  }
+  int a0, a1;
+  segment_range(offsets, act_scan, nsub3, n_t, seg, a0, a1);
+  seg_chunks[seg] = (a1 - a0 + kChunk - 1) / kChunk;
 }
 
 __global__ void k_write_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int n_t, int nsub3,
-                               const int* __restrict__ row_chunks, Chunk* __restrict__ chunks,
+                               const int* __restrict__ seg_chunks, Chunk* __restrict__ chunks,
                                int* __restrict__ n_chunks_out, int* __restrict__ n_active_out, int64_t n) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t rows = (int64_t)n_t * n_t;
-  if (r == 0) {
-    *n_chunks_out = row_chunks[rows];
+  const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nsegs = (int64_t)n_t * n_t * ((n_t + kChunkSpan - 1) / kChunkSpan);
+  if (seg == 0) {
+    *n_chunks_out = seg_chunks[nsegs];
     if (n_active_out) *n_active_out = act_scan ? act_scan[n] : (int)n;
   }
-  if (r >= rows) return;
-  walk_row(offsets, act_scan, nsub3, n_t, r, chunks + row_chunks[r]);
+  if (seg >= nsegs) return;
+  int a0, a1;
+  segment_range(offsets, act_scan, nsub3, n_t, seg, a0, a1);
+  Chunk* out = chunks + seg_chunks[seg];
+  for (int k = 0; a0 + k * kChunk < a1; ++k) {
+    const int s0 = a0 + k * kChunk;
+    out[k] = Chunk{s0, min(kChunk, a1 - s0)};
+  }
 }
 
 // Masked abar for the VJP: abar_i * [i active].
@@ -568,11 +570,49 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
     enumerate_suppliers<float>(a, F, S.L, lane, [&](int nlist, int total) {
       float* sxy = (float*)S.sxy;
       float* sz = (float*)S.sz;
+      const WarpList& L = S.L;
+      // Supplier f = b + lane of batch b lies in list entry e_cur + (number of
+      // entries starting in (b, b + lane]); the start positions of the next 32
+      // entries are gathered into one bit mask with a warp OR-reduction.
+      int e_cur = 0;  // entry holding position b
+      auto locate = [&](int b, int& j, unsigned& dpk) -> bool {
+        const int ek = e_cur + 1 + lane;
+        const int pos = (ek < nlist) ? L.pre[ek] - b : 64;
+        const unsigned bit = (pos > 0 && pos < kWarp) ? (1u << pos) : 0u;
+        const unsigned starts = __reduce_or_sync(full, bit);
+        const bool at_end = __any_sync(full, pos == kWarp);
+        const unsigned upto = (lane == kWarp - 1) ? 0xffffffffu : ((2u << lane) - 1u);
+        const int e = e_cur + __popc(starts & upto);
+        e_cur += __popc(starts) + (at_end ? 1 : 0);
+        const bool have = b + lane < total;
+        j = have ? L.start[e] + (b + lane - L.pre[e]) : 0;
+        dpk = have ? L.delta[e] : 0u;
+        return have;
+      };
+      // software pipeline: the record of batch b + 32 is loaded while batch b is evaluated
+      int jn;
+      unsigned dn;
+      bool vn = locate(0, jn, dn);
+      float4 rn = vn ? a.rel4[jn] : make_float4(0.f, 0.f, 0.f, 0.f);
       for (int b = 0; b < total; b += kWarp) {
-        const int f = b + lane;
-        Vec3<float> pj = {0.f, 0.f, 0.f}, aj;
+        const bool have = vn;
+        const float4 r = rn;
+        const unsigned dpk = dn;
+        vn = (b + kWarp < total) ? locate(b + kWarp, jn, dn) : false;
+        if (vn) rn = a.rel4[jn];
         bool keep = false;
-        if (f < total) keep = load_supplier<float, false>(a, S.L, nlist, f, F, pj, aj);
+        Vec3<float> pj = {0.f, 0.f, 0.f};
+        if (have) {
+          int dx, dy, dz;
+          unpack_delta(dpk, dx, dy, dz);
+          pj.x = fmaf((float)dx, a.g.side32[0], r.x);
+          pj.y = fmaf((float)dy, a.g.side32[1], r.y);
+          pj.z = fmaf((float)dz, a.g.side32[2], r.z);
+          const float tx = fmaxf(fmaxf(F.lo.x - pj.x, pj.x - F.hi.x), 0.f);
+          const float ty = fmaxf(fmaxf(F.lo.y - pj.y, pj.y - F.hi.y), 0.f);
+          const float tz = fmaxf(fmaxf(F.lo.z - pj.z, pj.z - F.hi.z), 0.f);
+          keep = fmaf(tx, tx, fmaf(ty, ty, tz * tz)) < a.f.margin2_f;
+        }
         const unsigned m = __ballot_sync(full, keep);
         const int nsurv = __popc(m);
         if (keep) {
@@ -602,15 +642,17 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
           const bool h0 = q0 < xr2, h1 = q1 < xr2;
           if (__any_sync(full, h0 || h1)) {
             hits += (int)h0 + (int)h1;
+            // r^2 = 0 (the receiver itself, coincident particles) contributes nothing;
+            // lanes that do not use a half drop its (possibly non-finite) value below
             const bool u0 = h0 && q0 > 0.0f, u1 = h1 && q1 > 0.0f;
-            f2 B = bracket_main_f32x2<SOFT>(pk(u0 ? q0 : 1.0f, u1 ? q1 : 1.0f), a.f);
+            f2 B = bracket_main_f32x2<SOFT>(r2, a.f);
             float b0, b1;
             upk(B, b0, b1);
             const bool rare0 = u0 && (q0 < a.f.rsw2_f), rare1 = u1 && (q1 < a.f.rsw2_f);
             if (__any_sync(full, rare0 || rare1)) {
               float Ds;
-              const float s0 = bracket_soft_f32<SOFT, false>(u0 ? q0 : 1.0f, a.f, a.sc, Ds);
-              const float s1 = bracket_soft_f32<SOFT, false>(u1 ? q1 : 1.0f, a.f, a.sc, Ds);
+              const float s0 = bracket_soft_f32<SOFT, false>(q0, a.f, a.sc, Ds);
+              const float s1 = bracket_soft_f32<SOFT, false>(q1, a.f, a.sc, Ds);
               if (rare0) b0 = s0;
               if (rare1) b1 = s1;
             }
@@ -630,6 +672,132 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
     upk(ay, l, h);
     acc.y = l + h;
     upk(az, l, h);
+    acc.z = l + h;
+    store_result<float>(a, F, acc);
+    hits = F.valid ? hits - 1 : 0;  // the receiver met itself once (r = 0)
+    pair_total += (unsigned long long)__reduce_add_sync(full, (unsigned)hits);
+  }
+  if (lane == 0 && pair_total) atomicAdd(a.pairs, pair_total);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 adjoint, packed broadcast: as k_force_packed, with every particle a
+// receiver and the masked abar of each supplier staged beside its position.
+//   xbar_k = -G m sum_j [ B v + (B'/r) (x_kj . v) x_kj ],  v = abar_k - abar_j.
+// ---------------------------------------------------------------------------
+
+struct PackedVjpSmem {
+  WarpList L;
+  float4 sxy[kWarp / 2 + 1];  // (-xa, -xb, -ya, -yb)
+  float2 sz[kWarp / 2 + 1];   // (-za, -zb)
+  float4 vxy[kWarp / 2 + 1];  // (-abar_xa, -abar_xb, -abar_ya, -abar_yb)
+  float2 vz[kWarp / 2 + 1];   // (-abar_za, -abar_zb)
+};
+
+template <int SOFT>
+__global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_vjp_packed(TraversalArgs a) {
+  __shared__ PackedVjpSmem smem[kPWarps];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  PackedVjpSmem& S = smem[threadIdx.x >> 5];
+  const int n_chunks = *a.n_chunks;
+  const float xr2 = a.f.xr2_f;
+  unsigned long long pair_total = 0;
+  for (;;) {
+    const int c = next_chunk(a, lane);
+    if (c >= n_chunks) break;
+    ChunkFrame<float> F;
+    load_chunk<float>(a, a.chunks[c], lane, F);
+    const f2 px = pk(F.pi.x, F.pi.x), py = pk(F.pi.y, F.pi.y), pz = pk(F.pi.z, F.pi.z);
+    float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (F.valid) ab = a.abar4[F.pidx];
+    const f2 vix = pk(ab.x, ab.x), viy = pk(ab.y, ab.y), viz = pk(ab.z, ab.z);
+    f2 gx = pk(0.f, 0.f), gy = pk(0.f, 0.f), gz = pk(0.f, 0.f);
+    int hits = 0;
+    enumerate_suppliers<float>(a, F, S.L, lane, [&](int nlist, int total) {
+      float* sxy = (float*)S.sxy;
+      float* sz = (float*)S.sz;
+      float* vxy = (float*)S.vxy;
+      float* vz = (float*)S.vz;
+      for (int b = 0; b < total; b += kWarp) {
+        const int f = b + lane;
+        Vec3<float> pj = {0.f, 0.f, 0.f}, aj = {0.f, 0.f, 0.f};
+        bool keep = false;
+        if (f < total) keep = load_supplier<float, true>(a, S.L, nlist, f, F, pj, aj);
+        const unsigned m = __ballot_sync(full, keep);
+        const int nsurv = __popc(m);
+        if (keep) {
+          const int k = __popc(m & ((1u << lane) - 1u));
+          const int p = k >> 1, h = k & 1;
+          sxy[4 * p + h] = -pj.x;
+          sxy[4 * p + 2 + h] = -pj.y;
+          sz[2 * p + h] = -pj.z;
+          vxy[4 * p + h] = -aj.x;
+          vxy[4 * p + 2 + h] = -aj.y;
+          vz[2 * p + h] = -aj.z;
+        }
+        if (lane == 0 && (nsurv & 1)) {  // pad the last pair far from every receiver
+          const int p = nsurv >> 1;
+          sxy[4 * p + 1] = 1e30f;
+          sxy[4 * p + 3] = 1e30f;
+          sz[2 * p + 1] = 1e30f;
+          vxy[4 * p + 1] = 0.f;
+          vxy[4 * p + 3] = 0.f;
+          vz[2 * p + 1] = 0.f;
+        }
+        __syncwarp();
+        const int npairs = (nsurv + 1) >> 1;
+        for (int p = 0; p < npairs; ++p) {
+          const float4 s = S.sxy[p];
+          const float2 z = S.sz[p];
+          const f2 dx = add2(px, pk(s.x, s.y));
+          const f2 dy = add2(py, pk(s.z, s.w));
+          const f2 dz = add2(pz, pk(z.x, z.y));
+          const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+          float q0, q1;
+          upk(r2, q0, q1);
+          const bool h0 = q0 < xr2, h1 = q1 < xr2;
+          if (__any_sync(full, h0 || h1)) {
+            hits += (int)h0 + (int)h1;
+            const float4 w = S.vxy[p];
+            const float2 wz = S.vz[p];
+            const f2 vx = add2(vix, pk(w.x, w.y));
+            const f2 vy = add2(viy, pk(w.z, w.w));
+            const f2 vz2 = add2(viz, pk(wz.x, wz.y));
+            // r = 0 in the adjoint: the receiver itself has v = 0; coincident distinct
+            // particles take the softened value B(0) (zero for point particles)
+            f2 D;
+            f2 B = bracket_main_vjp_f32x2<SOFT>(r2, a.f, D);
+            float b0, b1, d0, d1;
+            upk(B, b0, b1);
+            upk(D, d0, d1);
+            const bool rare0 = h0 && (q0 < a.f.rsw2_f), rare1 = h1 && (q1 < a.f.rsw2_f);
+            if (__any_sync(full, rare0 || rare1)) {
+              float Ds0, Ds1;
+              const float s0 = bracket_soft_f32<SOFT, true>(q0, a.f, a.sc, Ds0);
+              const float s1 = bracket_soft_f32<SOFT, true>(q1, a.f, a.sc, Ds1);
+              if (rare0) { b0 = s0; d0 = Ds0; }
+              if (rare1) { b1 = s1; d1 = Ds1; }
+            }
+            B = pk(h0 ? b0 : 0.0f, h1 ? b1 : 0.0f);
+            D = pk(h0 ? d0 : 0.0f, h1 ? d1 : 0.0f);
+            const f2 xv = fma2(dx, vx, fma2(dy, vy, mul2(dz, vz2)));
+            const f2 cc = mul2(D, xv);
+            gx = fma2(B, vx, fma2(cc, dx, gx));
+            gy = fma2(B, vy, fma2(cc, dy, gy));
+            gz = fma2(B, vz2, fma2(cc, dz, gz));
+          }
+        }
+        __syncwarp();
+      }
+    });
+    Vec3<float> acc;
+    float l, h;
+    upk(gx, l, h);
+    acc.x = l + h;
+    upk(gy, l, h);
+    acc.y = l + h;
+    upk(gz, l, h);
     acc.z = l + h;
     store_result<float>(a, F, acc);
     hits = F.valid ? hits - 1 : 0;  // the receiver met itself once (r = 0)
@@ -665,11 +833,13 @@ static SeriesConsts make_series() {
 
 template <class Real, bool VJP, int SOFT>
 static cudaError_t launch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
-  constexpr bool packed = (sizeof(Real) == 4) && !VJP;  // FP32 forward: packed broadcast kernel
+  constexpr bool packed = (sizeof(Real) == 4);  // FP32: packed broadcast kernels
   static int blocks_per_sm = 0;
   if (blocks_per_sm == 0) {
-    if (packed)
+    if (packed && !VJP)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_force_packed<SOFT>, kPThreads, 0);
+    else if (packed)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_vjp_packed<SOFT>, kPThreads, 0);
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_traverse<Real, VJP, SOFT>, kForceThreads, 0);
     if (blocks_per_sm < 1) blocks_per_sm = 1;
@@ -677,8 +847,10 @@ static cudaError_t launch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
   unsigned grid = (unsigned)(ctx->num_sms * blocks_per_sm);
   const int slot = VJP ? 1 : 0;
   cudaEventRecord(ctx->kt_ev[2 * slot], ctx->stream);
-  if (packed)
+  if (packed && !VJP)
     k_force_packed<SOFT><<<grid, kPThreads, 0, ctx->stream>>>(a);
+  else if (packed)
+    k_vjp_packed<SOFT><<<grid, kPThreads, 0, ctx->stream>>>(a);
   else
     k_traverse<Real, VJP, SOFT><<<grid, kForceThreads, 0, ctx->stream>>>(a);
   ++ctx->launches;
@@ -700,7 +872,7 @@ static p3m_status build_chunks(p3m_sr_ctx* ctx, const int* act_scan, Chunk* chun
                                int* n_active_dev) {
   cudaStream_t s = ctx->stream;
   const int n_t = ctx->geo.n_t;
-  const int64_t rows = (int64_t)n_t * n_t;
+  const int64_t rows = (int64_t)n_t * n_t * ((n_t + kChunkSpan - 1) / kChunkSpan);  // segments
   k_row_chunks<<<blocks_for(rows + 1, 128), 128, 0, s>>>(ctx->offsets, act_scan, n_t, ctx->geo.nsub3,
                                                          ctx->tile_chunks);
   ++ctx->launches;
@@ -872,7 +1044,7 @@ namespace p3m {
 
 constexpr int64_t kNoallocMaxN = 1 << 16;         // particles
 constexpr int64_t kNoallocMaxSubtiles = 1 << 18;  // subtiles (n_t n_sub)^3
-constexpr int64_t kNoallocMaxRows = 1 << 14;      // tile rows n_t^2
+constexpr int64_t kNoallocMaxRows = 1 << 14;      // chunk segments n_t^2 ceil(n_t / 4)
 constexpr int64_t kNoallocRadixBlocks = (kNoallocMaxN + kRadixTilePublic - 1) / kRadixTilePublic;
 constexpr int64_t kNoallocMaxChunks = kNoallocMaxN + kNoallocMaxN / kChunk + 1;
 
@@ -928,7 +1100,9 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
   setup_geometry(&c);
   setup_force_consts(&c);
   const Geometry& g = c.geo;
-  if (g.S > kNoallocMaxSubtiles || (int64_t)g.n_t * g.n_t > kNoallocMaxRows) return P3M_ERR_INVALID;
+  if (g.S > kNoallocMaxSubtiles ||
+      (int64_t)g.n_t * g.n_t * ((g.n_t + kChunkSpan - 1) / kChunkSpan) > kNoallocMaxRows)
+    return P3M_ERR_INVALID;
   if (params->x_r > 2.0 * P3M_ERFCX_UMAX * params->x_s) return P3M_ERR_INVALID;
   if (n == 0) return P3M_OK;
   if (!pos || !acc_out) return P3M_ERR_INVALID;
@@ -995,7 +1169,7 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
   k_gather_pos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, perm, n, spos);
   k_rel4<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(spos, cell, n, g, rel4);
   // receiver chunks (all particles active)
-  const int64_t nrows = (int64_t)g.n_t * g.n_t;
+  const int64_t nrows = (int64_t)g.n_t * g.n_t * ((g.n_t + kChunkSpan - 1) / kChunkSpan);  // segments
   k_row_chunks<<<(unsigned)((nrows + 1 + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   if (!ok(scan_exclusive_i32(rows, rows, nrows + 1, scan, s, &launches))) return P3M_ERR_CUDA;

@@ -139,6 +139,45 @@ __device__ __forceinline__ f2 bracket_main_f32x2(f2 r2, const ForceConsts& f) {
   return B;
 }
 
+// Main branch for two pairs with the derivative (adjoint): returns B and sets
+// D = B'(r)/r for both halves.
+template <int SOFT>
+__device__ __forceinline__ f2 bracket_main_vjp_f32x2(f2 r2, const ForceConsts& f, f2& D) {
+  float a, b;
+  upk(r2, a, b);
+  const f2 rinv = pk(rsqrt_approx(a), rsqrt_approx(b));
+  const f2 r = mul2(r2, rinv);
+  float ea, eb;
+  upk(mul2(r2, pk(f.ce_f, f.ce_f)), ea, eb);
+  const f2 e = pk(ex2_approx(ea), ex2_approx(eb));
+  float da, db;
+  upk(fma2(r, pk(f.kc_f, f.kc_f), pk(1.0f, 1.0f)), da, db);
+  const f2 t = pk(rcp_approx(da), rcp_approx(db));
+  f2 q = fma2(pk(f.c_f[5], f.c_f[5]), t, pk(f.c_f[4], f.c_f[4]));
+  q = fma2(q, t, pk(f.c_f[3], f.c_f[3]));
+  q = fma2(q, t, pk(f.c_f[2], f.c_f[2]));
+  q = fma2(q, t, pk(f.c_f[1], f.c_f[1]));
+  q = fma2(q, t, pk(f.c_f[0], f.c_f[0]));
+  const f2 ex = mul2(q, t);
+  const f2 rinv2 = mul2(rinv, rinv);
+  const f2 er2 = mul2(e, rinv2);
+  f2 B = mul2(er2, fma2(ex, rinv, pk(f.k2_f, f.k2_f)));
+  // g'(r)/r = -r^{-2} (3 g + exp(-u^2) k3)
+  D = mul2(mul2(rinv2, pk(-1.0f, -1.0f)), fma2(pk(3.0f, 3.0f), B, mul2(e, pk(f.k3_f, f.k3_f))));
+  if (SOFT == P3M_SOFT_PLUMMER) {
+    float pa, pb;
+    upk(add2(r2, pk(f.eps2_f, f.eps2_f)), pa, pb);
+    const f2 p = pk(rsqrt_approx(pa), rsqrt_approx(pb));
+    const f2 p2 = mul2(p, p);
+    const f2 p3 = mul2(p2, p);
+    const f2 rinv3 = mul2(rinv2, rinv);
+    // D += 3 (r^-5 - p^5),  B += p^3 - r^-3
+    D = fma2(pk(3.0f, 3.0f), fma2(rinv3, rinv2, mul2(mul2(p3, p2), pk(-1.0f, -1.0f))), D);
+    B = add2(B, fma2(rinv3, pk(-1.0f, -1.0f), p3));
+  }
+  return B;
+}
+
 // Softened branch, r^2 < r_sw^2 (and r = 0 for point particles).
 template <int SOFT, bool VJP>
 __device__ __forceinline__ float bracket_soft_f32(float r2, const ForceConsts& f, const SeriesConsts& sc,

@@ -80,3 +80,4 @@ def test_n134m_sampled_with_rungs():
             if len(inact):
                 probe = torch.from_numpy(inact[:4096]).to(dev)
                 assert torch.isnan(out32[:, probe]).all()
+
