@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="n2m")
-    ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="receivers in the CPU-oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 18, help="receivers in the CPU-oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1 << 14, help="receivers per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["forces32", "forces64", "vjp32", "sort"], default=None,

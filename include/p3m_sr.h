@@ -165,7 +165,10 @@ p3m_status p3m_sr_build_pairs(p3m_sr_ctx* ctx, const int8_t* rung, int rung_min)
 /*
  * Short-range accelerations (Section 2.1.3, short-range half of Eq.
  * p3m_gravity) on the receivers of the last p3m_sr_build_pairs.
- *   pos        3 x n float64 SoA, device, in the sorted order.
+ *   pos        3 x n float64 SoA, device, in the sorted order and unchanged
+ *              since the last p3m_sr_sort (the sort already wrote the FP32
+ *              subtile-relative records of that array; a different array is
+ *              re-read here).
  *   precision  32: FP32 arithmetic and accumulation, displacements taken
  *              relative to subtile origins (positions read once in FP64);
  *              acc_out is 3 x n float.  64: FP64 throughout, acc_out 3 x n

@@ -60,6 +60,7 @@ struct p3m_sr_ctx {
 
   // ---- state ----
   bool sorted = false;
+  const double* sorted_pos = nullptr;  // array sorted by the last p3m_sr_sort (rel4 matches it)
   bool pairs_built = false;
   bool all_chunks_built = false;
   bool all_active = true;

@@ -911,6 +911,7 @@ static TraversalArgs base_args(p3m_sr_ctx* ctx) {
 
 static p3m_status prepare_rel4(p3m_sr_ctx* ctx, const double* pos) {
   if (ctx->n == 0) return P3M_OK;
+  if (pos == ctx->sorted_pos) return P3M_OK;  // written by the sort for these positions
   k_rel4<<<blocks_for(ctx->n, 256), 256, 0, ctx->stream>>>(pos, ctx->cell, ctx->n, ctx->geo, ctx->rel4);
   ++ctx->launches;
   return cuda_check(ctx, cudaGetLastError(), "rel4 kernel");

@@ -28,13 +28,21 @@ __global__ void k_bin(const double* __restrict__ pos, int64_t n, Geometry g, int
   if (valid) {
     int gc[3];
     bool bad = false;
+    const long long box_bits = __double_as_longlong(g.box);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       double v = pos[d * n + i];
-      bool ok = (v >= 0.0) && (v < g.box);  // false for NaN
+      // 0 <= v < L on the bit patterns (non-negative doubles order like integers;
+      // NaN, negative values and v >= L all fail)
+      const long long vb = __double_as_longlong(v);
+      bool ok = (vb >= 0) && (vb < box_bits);
       bad |= !ok;
       double p = __dmul_rn(ok ? v : 0.0, g.scale64[d]);
-      int q = (int)p;  // p >= 0: truncation is floor
+      // floor(p) for 0 <= p < 2^31 from the exponent and mantissa bits
+      const long long pb = __double_as_longlong(p);
+      const int e = (int)(pb >> 52) - 1023;
+      int q = 0;
+      if (e >= 0) q = (int)((((pb & 0xfffffffffffffLL) | (1LL << 52)) >> (52 - e)));
       gc[d] = q < g.M[d] - 1 ? q : g.M[d] - 1;
     }
     if (bad) atomicOr(err, kErrPosition);
@@ -129,6 +137,25 @@ __global__ void k_gather_pos(const double* __restrict__ src, const int* __restri
   dst[k] = src[j];
   dst[n + k] = src[n + j];
   dst[2 * n + k] = src[2 * n + j];
+}
+
+// Gather the positions into walk order and write the FP32 record of each
+// particle: its coordinates relative to the origin of its subtile and the id.
+__global__ void k_gather_pos_rel4(const double* __restrict__ src, const int* __restrict__ perm,
+                                  const int* __restrict__ cell, int64_t n, Geometry g, double* __restrict__ dst,
+                                  float4* __restrict__ rel4) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int64_t j = perm[k];
+  const double x = src[j], y = src[n + j], z = src[2 * n + j];
+  dst[k] = x;
+  dst[n + k] = y;
+  dst[2 * n + k] = z;
+  const int id = cell[k];
+  int gx, gy, gz;
+  decode_subtile(g, id, gx, gy, gz);
+  rel4[k] = make_float4((float)__fma_rn(-(double)gx, g.side64[0], x), (float)__fma_rn(-(double)gy, g.side64[1], y),
+                        (float)__fma_rn(-(double)gz, g.side64[2], z), __int_as_float(id));
 }
 
 template <class T>
@@ -234,7 +261,7 @@ extern "C" p3m_status p3m_sr_sort(p3m_sr_ctx* ctx, double* pos, void* const* car
   ctx->perm = ctx->vals[cur];
   if (n > 0) {
     double* tmp = (double*)ctx->gather_tmp;
-    k_gather_pos<<<blocks_for(n, 256), 256, 0, s>>>(pos, ctx->perm, n, tmp);
+    k_gather_pos_rel4<<<blocks_for(n, 256), 256, 0, s>>>(pos, ctx->perm, ctx->cell, n, g, tmp, ctx->rel4);
     ++ctx->launches;
     if ((st = cuda_check(ctx, cudaGetLastError(), "gather positions")) != P3M_OK) return st;
     st = cuda_check(ctx, cudaMemcpyAsync(pos, tmp, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy");
@@ -252,6 +279,7 @@ extern "C" p3m_status p3m_sr_sort(p3m_sr_ctx* ctx, double* pos, void* const* car
   }
   report_latched(ctx);
   ctx->sorted = true;
+  ctx->sorted_pos = pos;  // the FP32 records in ctx->rel4 describe these positions
   return P3M_OK;
 }
 

@@ -65,7 +65,8 @@ __global__ void k_drift(double* __restrict__ pos, const M* __restrict__ mom, int
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     double v = __dadd_rn(pos[d * n + i], __dmul_rn((double)mom[d * n + i], factor));
-    if (v < 0.0 || v >= box) {  // v - L floor(v / L); floor is 0 inside the box
+    const long long vb = __double_as_longlong(v);
+    if (!(vb >= 0 && vb < __double_as_longlong(box))) {  // v - L floor(v / L); floor is 0 inside the box
       v = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
       if (v >= box || v < 0.0) v = 0.0;
     }
@@ -149,5 +150,6 @@ extern "C" p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom
                                                                  ctx->prm.box); ++ctx->launches; }
   ctx->pairs_built = false;  // positions moved: the tiling must be rebuilt
   ctx->sorted = false;
+  ctx->sorted_pos = nullptr;
   return cuda_check(ctx, cudaGetLastError(), "drift kernel");
 }

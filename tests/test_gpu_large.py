@@ -81,3 +81,49 @@ def test_n134m_sampled_with_rungs():
                 probe = torch.from_numpy(inact[:4096]).to(dev)
                 assert torch.isnan(out32[:, probe]).all()
 
+
+def test_n1g_sampled():
+    """1024^3: the FP32 forces of all particles, and the FP64 forces of the deepest
+    rung (~1% active), on 2^18 sampled receivers against the oracle; rungs
+    bit-exact on the sample."""
+    w = synth.workload("n1g")
+    n = w.n
+    pos = synth.workload_positions(w)
+    dev = torch.device("cuda")
+    eta = 0.025
+    rng = np.random.default_rng(11)
+    with ShortRange.from_workload(w) as sr:
+        p = torch.from_numpy(pos).to(dev)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        sr.sort(p, perm_out=perm)
+        sr.build_pairs()
+        a32 = sr.forces(p, 32)
+        st = sr.stats()
+        print(f"n1g: {st.pairs_last} interacting pairs, FP32 kernel {st.force_kernel_ms:.1f} ms")
+        amag = torch.linalg.vector_norm(a32, dim=0)
+        sample = torch.randperm(n, device=dev, generator=torch.Generator(device=dev).manual_seed(0))[:1 << 20]
+        q99 = float(torch.quantile(amag[sample], 0.99))
+        del amag
+        dt = 64.0 * (2.0 * eta * w.eps / q99) ** 0.5
+        rung = sr.assign_rungs(a32, dt, eta, w.eps)
+        k32 = np.sort(rng.choice(n, size=1 << 18, replace=False))
+        kk = torch.from_numpy(k32).to(dev)
+        g32 = a32[:, kk].cpu().numpy()
+        ref_r, _ = oracle.rungs(g32.astype(np.float64), dt, eta, w.eps, 8)
+        np.testing.assert_array_equal(rung[kk].cpu().numpy(), ref_r)
+        sr.build_pairs(rung, 7)
+        a64 = torch.full((3, n), float("nan"), dtype=torch.float64, device=dev)
+        sr.forces(p, 64, a64)
+        st = sr.stats()
+        act = torch.nonzero(rung >= 7).flatten()
+        k64 = act[torch.randperm(len(act), device=dev, generator=torch.Generator(device=dev).manual_seed(1))[:1 << 18]]
+        k64 = torch.sort(k64).values
+        g64 = a64[:, k64].cpu().numpy()
+        perm_np = perm.cpu().numpy().astype(np.int64)
+        assert st.n_active == len(act)
+    del p
+    for name, ks, got, tol in (("fp32", k32, g32, 1e-5), ("fp64 rung 7", k64.cpu().numpy(), g64, 1e-12)):
+        ref, _ = oracle.sr_accel_subset(pos, perm_np[ks], w.x_s, w.x_r, w.G_m, "bspline", w.eps)
+        err = rel_rms(got, ref)
+        print(f"n1g {name}: rel RMS {err:.3e} over {len(ks)} receivers")
+        assert err <= tol
