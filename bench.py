@@ -45,7 +45,7 @@ OPS_PER_PAIR = 26  # FP32 pipe instructions per interacting pair fixed for the r
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="n2m")
@@ -303,6 +303,31 @@ def run_ours(args):
     a32 = acc.double()
     parity_32_64 = float(torch.sqrt(((a32 - acc64) ** 2).sum() / (acc64 ** 2).sum()))
     fp64_rate = fp64_pairs / (statistics.mean(fp64_ms) * 1e-3)
+    # the paper's tabulated bracket (2^12 NGP bins in r^2) on the same state
+    tab_ms = []
+    acc_tab = torch.zeros_like(acc)
+    for _ in range(3):
+        flush.zero_()
+        sr.forces_tabulated(pos, 12, acc_tab)
+        st = sr.stats()
+        tab_ms.append(st.force_kernel_ms)
+    tab_err = float(torch.sqrt(((acc_tab.double() - acc64) ** 2).sum() / (acc64 ** 2).sum()))
+    tabulated = {"value": st.pairs_last / (statistics.mean(tab_ms) * 1e-3), "unit": UNIT,
+                 "kernel_ms": statistics.mean(tab_ms), "rel_rms_vs_fp64": tab_err, "table_entries": 4096}
+    # subtiles per tile (Section 2.1.3 "Subtiles"; the paper compares fixed 1^3 ... 9^3)
+    sweep = {}
+    pos_s = pos.clone()
+    for ns in (1, 2, 3, 4):
+        with ShortRange.from_workload(w, device=dev, n_sub=ns) as s2:
+            s2.sort(pos_s)
+            s2.build_pairs()
+            ts = []
+            for _ in range(3):
+                flush.zero_()
+                s2.forces(pos_s, 32, acc_tab)
+                ts.append(s2.stats().force_kernel_ms)
+            sweep[str(ns)] = statistics.mean(ts)
+    del pos_s
 
     # end to end through the public API with host buffers
     e2e_ms, e2e_pairs = [], []
@@ -348,6 +373,8 @@ def run_ours(args):
             "fp32_over_fp64": achieved / fp64_rate,
             "fp32_vs_fp64_rel_rms": parity_32_64,
             "adjoint_over_forward": statistics.mean(vjp_ms) / statistics.mean(fwd_ms),
+            "tabulated_2p12": tabulated,
+            "n_sub_sweep_force_ms": sweep,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * 8 * n,

@@ -179,6 +179,19 @@ p3m_status p3m_sr_build_pairs(p3m_sr_ctx* ctx, const int8_t* rung, int rung_min)
 p3m_status p3m_sr_forces(p3m_sr_ctx* ctx, const double* pos, int precision, void* acc_out);
 
 /*
+ * The paper's tabulated variant of the FP32 forces (Section 2.1.3, "Other
+ * optimisations": the bracket of Eq. p3m_gravity, softening included, stored in
+ * a 1-D table indexed by r^2 on [0, x_r^2) and read with a nearest-grid-point
+ * lookup; the paper uses 2^12 entries).  Same receivers, traversal and output
+ * as p3m_sr_forces with precision 32; only B(r) comes from the table, built in
+ * FP64 at the bin centres on the first call with a given table_bits (4..14).
+ * Its error is far above the analytic path's (see the tests); it exists to
+ * measure the paper's speed/accuracy trade-off on this hardware.
+ *   acc_out  3 x n float; receivers' rows are overwritten.
+ */
+p3m_status p3m_sr_forces_tabulated(p3m_sr_ctx* ctx, const double* pos, int table_bits, float* acc_out);
+
+/*
  * Rungs from accelerations (Section 2.2.2, Eq. rung):
  *   l_i = max(0, ceil(log2(dt sqrt(|a_i| / (2 eta eps))))), clamped to n_rung-1,
  * evaluated exactly as: q = dt*dt / ((2*eta)*eps); s = (q*q) * ((ax*ax + ay*ay) + az*az);

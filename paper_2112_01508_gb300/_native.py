@@ -33,7 +33,7 @@ SOFTENING = {"none": 0, "plummer": 1, "bspline": 2}
 EXPORTS = (
     "p3m_sr_create", "p3m_sr_destroy", "p3m_sr_last_error", "p3m_sr_sync", "p3m_sr_stats", "p3m_sr_sort",
     "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
-    "p3m_sr_permute", "p3m_sr_unpermute", "p3m_sr_forces_noalloc",
+    "p3m_sr_permute", "p3m_sr_unpermute", "p3m_sr_forces_noalloc", "p3m_sr_forces_tabulated",
 )
 
 
@@ -121,6 +121,8 @@ def load() -> ctypes.CDLL:
         L.p3m_sr_unpermute.restype = i
         L.p3m_sr_forces_noalloc.argtypes = [ctypes.POINTER(P3MParams), p, p, p]
         L.p3m_sr_forces_noalloc.restype = i
+        L.p3m_sr_forces_tabulated.argtypes = [p, p, i, p]
+        L.p3m_sr_forces_tabulated.restype = i
         _lib = L
         return L
 
@@ -195,3 +197,7 @@ def p3m_sr_permute(ctx, src_ptr, dst_ptr, elem_bytes, rows) -> int:
 def p3m_sr_unpermute(ctx, src_ptr, dst_ptr, elem_bytes, rows) -> int:
     return load().p3m_sr_unpermute(ctx, ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr), int(elem_bytes),
                                    int(rows))
+
+
+def p3m_sr_forces_tabulated(ctx, pos_ptr, table_bits, acc_ptr) -> int:
+    return load().p3m_sr_forces_tabulated(ctx, ctypes.c_void_p(pos_ptr), int(table_bits), ctypes.c_void_p(acc_ptr))

@@ -45,6 +45,8 @@ struct p3m_sr_ctx {
   float4* rel4 = nullptr;             // FP32 subtile-relative coordinates (+ id bits)
   float4* abar4 = nullptr;            // vjp: masked abar, FP32
   double* abar_d = nullptr;           // vjp: masked abar, FP64 (3 n)
+  float* table = nullptr;             // tabulated bracket (p3m_sr_forces_tabulated)
+  int table_bits = 0;
 
   // ---- error latch ----
   int* err_dev = nullptr;

@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "ctx.cuh"
 #include "erfcx_fit.h"
@@ -186,6 +187,11 @@ struct TraversalArgs {
   const float4* abar4;        // masked abar FP32
   const double* abar_d;       // masked abar FP64, 3 x n
   unsigned long long* pairs;  // interacting ordered pairs
+  // tabulated bracket (p3m_sr_forces_tabulated): B at the centres of n_table
+  // equal bins of r^2 in [0, x_r^2)
+  const float* table;
+  int n_table;
+  float table_scale;          // n_table / x_r^2
 };
 
 template <class Real>
@@ -549,9 +555,14 @@ struct PackedSmem {
 #define P3M_GP_MINBLOCKS 6
 #endif
 
-template <int SOFT>
+template <int SOFT, bool TABLE = false>
 __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(TraversalArgs a) {
   __shared__ PackedSmem smem[kPWarps];
+  extern __shared__ float tab[];  // TABLE: the bracket table (n_table floats)
+  if (TABLE) {
+    for (int i = threadIdx.x; i < a.n_table; i += blockDim.x) tab[i] = a.table[i];
+    __syncthreads();
+  }
 
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -645,18 +656,25 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
             // r^2 = 0 (the receiver itself, coincident particles) contributes nothing;
             // lanes that do not use a half drop its (possibly non-finite) value below
             const bool u0 = h0 && q0 > 0.0f, u1 = h1 && q1 > 0.0f;
-            f2 B = bracket_main_f32x2<SOFT>(r2, a.f);
             float b0, b1;
-            upk(B, b0, b1);
-            const bool rare0 = u0 && (q0 < a.f.rsw2_f), rare1 = u1 && (q1 < a.f.rsw2_f);
-            if (__any_sync(full, rare0 || rare1)) {
-              float Ds;
-              const float s0 = bracket_soft_f32<SOFT, false>(q0, a.f, a.sc, Ds);
-              const float s1 = bracket_soft_f32<SOFT, false>(q1, a.f, a.sc, Ds);
-              if (rare0) b0 = s0;
-              if (rare1) b1 = s1;
+            if (TABLE) {  // nearest-grid-point lookup in r^2 (softening included)
+              const int i0 = min((int)(fminf(q0, a.f.xr2_f) * a.table_scale), a.n_table - 1);
+              const int i1 = min((int)(fminf(q1, a.f.xr2_f) * a.table_scale), a.n_table - 1);
+              b0 = tab[max(i0, 0)];
+              b1 = tab[max(i1, 0)];
+            } else {
+              f2 B = bracket_main_f32x2<SOFT>(r2, a.f);
+              upk(B, b0, b1);
+              const bool rare0 = u0 && (q0 < a.f.rsw2_f), rare1 = u1 && (q1 < a.f.rsw2_f);
+              if (__any_sync(full, rare0 || rare1)) {
+                float Ds;
+                const float s0 = bracket_soft_f32<SOFT, false>(q0, a.f, a.sc, Ds);
+                const float s1 = bracket_soft_f32<SOFT, false>(q1, a.f, a.sc, Ds);
+                if (rare0) b0 = s0;
+                if (rare1) b1 = s1;
+              }
             }
-            B = pk(u0 ? b0 : 0.0f, u1 ? b1 : 0.0f);
+            const f2 B = pk(u0 ? b0 : 0.0f, u1 ? b1 : 0.0f);
             ax = fma2(B, dx, ax);
             ay = fma2(B, dy, ay);
             az = fma2(B, dz, az);
@@ -974,6 +992,101 @@ extern "C" p3m_status p3m_sr_forces(p3m_sr_ctx* ctx, const double* pos, int prec
   a.out = acc_out;
   cudaError_t e = (precision == 32) ? dispatch_traverse<float, false>(ctx, a) : dispatch_traverse<double, false>(ctx, a);
   if ((st = cuda_check(ctx, e, "force kernel")) != P3M_OK) return st;
+  report_latched(ctx);
+  return P3M_OK;
+}
+
+// B(r) in double on the host, for the table of p3m_sr_forces_tabulated.
+static double bracket_host(double r, const ForceConsts& f, const SeriesConsts& sc) {
+  const double inv_sqrt_pi = 0.56418958354775628695;
+  const double r2 = r * r;
+  if (r < f.r_sw) {
+    if (f.softening == P3M_SOFT_NONE) return 0.0;
+    const double u = r / (2.0 * f.x_s), u2 = u * u, w = 2.0 * f.x_s;
+    double h = sc.h_d[kHTermsD - 1];
+    for (int k = kHTermsD - 2; k >= 0; --k) h = h * u2 + sc.h_d[k];
+    double s3;
+    if (f.softening == P3M_SOFT_BSPLINE) {
+      const double x = r / f.eps_b, c = 32.0 / (f.eps_b * f.eps_b * f.eps_b);
+      s3 = (x < 0.5) ? c * (x * x * x - 1.2 * x * x + 1.0 / 3.0)
+                     : c * (-x * x * x / 3.0 + 1.2 * x * x - 1.5 * x + 2.0 / 3.0 - 1.0 / (480.0 * x * x * x));
+    } else {
+      const double p = 1.0 / std::sqrt(r2 + f.eps * f.eps);
+      s3 = p * p * p;
+    }
+    return s3 - h / (w * w * w);
+  }
+  const double u = r / (2.0 * f.x_s);
+  double B = (std::erfc(u) + 2.0 * inv_sqrt_pi * u * std::exp(-u * u)) / (r2 * r);
+  if (f.softening == P3M_SOFT_PLUMMER) {
+    const double p = 1.0 / std::sqrt(r2 + f.eps * f.eps);
+    B += p * p * p - 1.0 / (r2 * r);
+  }
+  return B;
+}
+
+extern "C" p3m_status p3m_sr_forces_tabulated(p3m_sr_ctx* ctx, const double* pos, int table_bits, float* acc_out) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (table_bits < 4 || table_bits > 14) return fail(ctx, P3M_ERR_INVALID, "forces_tabulated: table_bits must be 4..14");
+  if (ctx->n > 0 && (!pos || !acc_out)) return fail(ctx, P3M_ERR_INVALID, "forces_tabulated: null pointer");
+  if (!ctx->sorted || !ctx->pairs_built)
+    return fail(ctx, P3M_ERR_STATE, "forces_tabulated: call p3m_sr_sort and p3m_sr_build_pairs first");
+  p3m_status st = poll_latched(ctx);
+  if (st != P3M_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const int nt = 1 << table_bits;
+  if (ctx->table_bits != table_bits) {
+    static SeriesConsts series = make_series();
+    std::vector<float> h(nt);
+    for (int i = 0; i < nt; ++i) {
+      const double r2c = (i + 0.5) * ctx->prm.x_r * ctx->prm.x_r / nt;  // bin centre in r^2
+      h[i] = (float)bracket_host(std::sqrt(r2c), ctx->fc, series);
+    }
+    if (ctx->table) {
+      cudaStreamSynchronize(s);
+      cudaFree(ctx->table);
+      ctx->table = nullptr;
+    }
+    if ((st = cuda_check(ctx, cudaMalloc((void**)&ctx->table, sizeof(float) * nt), "cudaMalloc(table)")) != P3M_OK)
+      return st;
+    if ((st = cuda_check(ctx, cudaMemcpy(ctx->table, h.data(), sizeof(float) * nt, cudaMemcpyHostToDevice),
+                         "table copy")) != P3M_OK)
+      return st;
+    ctx->table_bits = table_bits;
+  }
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->pair_count, 0, sizeof(unsigned long long), s), "memset")) != P3M_OK)
+    return st;
+  if (ctx->n == 0) return P3M_OK;
+  if ((st = prepare_rel4(ctx, pos)) != P3M_OK) return st;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dev_small + 3, 0, sizeof(int), s), "memset")) != P3M_OK) return st;
+  TraversalArgs a = base_args(ctx);
+  a.pos = pos;
+  a.chunks = ctx->chunks;
+  a.n_chunks = ctx->dev_small + 0;
+  a.counter = ctx->dev_small + 3;
+  a.active_idx = ctx->all_active ? nullptr : ctx->active_idx;
+  a.out = acc_out;
+  a.table = ctx->table;
+  a.n_table = nt;
+  a.table_scale = (float)(nt / (ctx->prm.x_r * ctx->prm.x_r));
+  const size_t shm = sizeof(float) * nt;
+  auto launch = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPThreads, shm);
+    const unsigned grid = (unsigned)(ctx->num_sms * (bps > 0 ? bps : 1));
+    cudaEventRecord(ctx->kt_ev[0], s);
+    kern<<<grid, kPThreads, shm, s>>>(a);
+    ++ctx->launches;
+    cudaEventRecord(ctx->kt_ev[1], s);
+    ctx->kt_pending[0] = true;
+  };
+  switch (ctx->prm.softening) {
+    case P3M_SOFT_NONE: launch(k_force_packed<P3M_SOFT_NONE, true>); break;
+    case P3M_SOFT_PLUMMER: launch(k_force_packed<P3M_SOFT_PLUMMER, true>); break;
+    default: launch(k_force_packed<P3M_SOFT_BSPLINE, true>); break;
+  }
+  if ((st = cuda_check(ctx, cudaGetLastError(), "tabulated force kernel")) != P3M_OK) return st;
   report_latched(ctx);
   return P3M_OK;
 }

@@ -333,7 +333,7 @@ extern "C" void p3m_sr_destroy(p3m_sr_ctx* ctx) {
   void* ptrs[] = {ctx->keys[0], ctx->keys[1], ctx->vals[0], ctx->vals[1], ctx->offsets, ctx->hist,
                   ctx->scan_scratch, ctx->gather_tmp, ctx->active_flag, ctx->act_scan, ctx->active_idx,
                   ctx->tile_chunks, ctx->chunks, ctx->chunks_all, ctx->dev_small, ctx->pair_count,
-                  ctx->rel4, ctx->abar4, ctx->abar_d, ctx->err_dev};
+                  ctx->rel4, ctx->abar4, ctx->abar_d, ctx->table, ctx->err_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->err_host) cudaFreeHost(ctx->err_host);

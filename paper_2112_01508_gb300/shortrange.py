@@ -139,6 +139,16 @@ class ShortRange:
         self._raise(nat.p3m_sr_forces(self._ctx, pos.data_ptr(), precision, out.data_ptr()))
         return out
 
+    def forces_tabulated(self, pos: torch.Tensor, table_bits: int = 12,
+                         out: torch.Tensor | None = None) -> torch.Tensor:
+        """FP32 forces with the bracket read from a 2^table_bits NGP table in r^2."""
+        _check(pos, "pos", torch.float64, (3, self.n), self.device)
+        if out is None:
+            out = torch.zeros((3, self.n), dtype=torch.float32, device=self.device)
+        _check(out, "out", torch.float32, (3, self.n), self.device)
+        self._raise(nat.p3m_sr_forces_tabulated(self._ctx, pos.data_ptr(), table_bits, out.data_ptr()))
+        return out
+
     def assign_rungs(self, acc: torch.Tensor, dt: float, eta: float, eps: float,
                      out: torch.Tensor | None = None) -> torch.Tensor:
         _check(acc, "acc", (torch.float32, torch.float64), (3, self.n), self.device)

@@ -147,3 +147,29 @@ def test_coincident_particles():
     pos = rng.random((3, 400))
     pos = np.concatenate([pos, pos[:, :50]], axis=1)  # 50 exact duplicates
     _edge_case(pos)
+
+
+def test_tabulated_variant_error(n32k):
+    """The paper's 2^12-entry NGP table in r^2 (Section 2.1.3): its force error is
+    reported and bounded loosely; more entries must be more accurate."""
+    pos, refs = n32k
+    ref, pairs = refs["bspline"]
+    from paper_2112_01508_gb300 import ShortRange
+    n = W1.n
+    errs = {}
+    with ShortRange.from_workload(W1) as sr:
+        p = torch.from_numpy(pos.copy()).cuda()
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+        sr.sort(p, perm_out=perm)
+        sr.build_pairs()
+        pm = perm.cpu().numpy().astype(np.int64)
+        for bits in (10, 12, 14):
+            out = sr.forces_tabulated(p, bits)
+            st = sr.stats()
+            got = np.empty((3, n))
+            got[:, pm] = out.cpu().numpy()
+            errs[bits] = rel_rms(got, ref)
+            assert abs(st.pairs_last - pairs) <= max(2, 1e-6 * pairs)
+    print("tabulated rel RMS:", errs)
+    assert errs[14] < errs[12] < errs[10]
+    assert errs[12] < 0.1  # ~6.5% on this set (3.8% on the 128^3 set)
