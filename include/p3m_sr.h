@@ -217,6 +217,35 @@ p3m_status p3m_sr_kick(p3m_sr_ctx* ctx, void* mom, int mom_precision, const void
                        const double* kick_factor);
 
 /*
+ * One kick of the rung-based leapfrog (Section 2.2.2, the time-stepping figure:
+ * rung-l momenta are kicked every dt / 2^l, positions drift every
+ * dt / 2^(n_rung-1); a particle whose rung changes jumps to a neighbouring rung
+ * by making its next kick 1/2 or 3/4 as large as usual, and can move to a lower
+ * rung only at every other kick).  For the particles with rung >= rung_min:
+ *   q_i <- q_i + a_i f_i dt / 2^l_i,   f_i = 1, 1/2 or 3/4 by kick_state_i (0, 1, 2);
+ * then, from the same a_i, the rung of Eq. rung (computed as in
+ * p3m_sr_assign_rungs) decides the jump:
+ *   higher than l_i -> l_i + 1, next kick 1/2 of the usual (state 1);
+ *   lower than l_i and substep / 2^(n_rung-1-l_i) odd -> l_i - 1, next kick 3/4
+ *   of the usual (state 2);  otherwise unchanged (state 0).
+ *   substep   global substep counter k >= 1: this kick happens at k dt / 2^(n_rung-1)
+ *             after the last synchronisation; rung_min must equal
+ *             n_rung - 1 - (trailing zero bits of k), capped at 0 (P3M_ERR_INVALID
+ *             otherwise).
+ *   synchronize  non-zero at the end of a global step (k a multiple of
+ *             2^(n_rung-1)): the kick stops at that time (factor f_i - 1/2), the
+ *             states are reset and the rungs are left for p3m_sr_assign_rungs.
+ *   mom, acc  3 x n device, precision 32 or 64; rung, kick_state  n int8 device,
+ *             updated in place.  Arithmetic in IEEE double as in p3m_sr_kick.
+ * A particle with rung >= n_rung or kick_state outside {0, 1, 2} is left
+ * untouched and latches P3M_ERR_STATE (reported by this or a later call, or
+ * by p3m_sr_sync); a non-finite acceleration latches P3M_ERR_NONFINITE.
+ */
+p3m_status p3m_sr_rung_kick(p3m_sr_ctx* ctx, void* mom, int mom_precision, const void* acc, int acc_precision,
+                            int8_t* rung, int8_t* kick_state, int rung_min, long long substep, double dt,
+                            double eta, double eps, int synchronize);
+
+/*
  * Drift (Section 2.2.2, operator D with a = 1):
  *   x_i <- x_i + q_i * factor, then wrapped into [0, L): x <- x - L floor(x / L).
  *   pos  3 x n float64 device;  mom  3 x n device, mom_precision 32 or 64.

@@ -70,6 +70,8 @@ def _load():
             lib.oracle_kick.restype = None
             lib.oracle_drift.argtypes = [i64, p, p, d, d]
             lib.oracle_drift.restype = None
+            lib.oracle_rung_kick.argtypes = [i64, p, p, p, p, i, ctypes.c_longlong, i, d, d, d, i]
+            lib.oracle_rung_kick.restype = i64
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = i
             _lib = lib
@@ -186,3 +188,43 @@ def drift(pos, mom, factor, box=1.0):
     mom = _f64(mom)
     _load().oracle_drift(pos.shape[1], _ptr(pos), _ptr(mom), factor, box)
     return pos
+
+
+def rung_kick(mom, acc, rung, state, rung_min, substep, n_rung, dt, eta, eps, sync=False):
+    """One kick of the rung-based leapfrog; mom, rung, state are updated in place."""
+    assert mom.dtype == np.float64 and mom.flags.c_contiguous
+    assert rung.dtype == np.int8 and state.dtype == np.int8
+    acc = _f64(acc)
+    return _load().oracle_rung_kick(mom.shape[1], _ptr(mom), _ptr(acc), _ptr(rung), _ptr(state), int(rung_min),
+                                    int(substep), int(n_rung), float(dt), float(eta), float(eps), int(bool(sync)))
+
+
+def rung_leapfrog(pos, mom, x_s, x_r, G_m, softening, eps, dt, eta, n_rung, n_steps, box=1.0):
+    """The rung-based KDK of Section 2.2.2 over n_steps global steps, synchronised
+    at the end: fake kick (forces of all particles, rungs of Eq. rung), half
+    kicks dt/2^(l+1) per rung, then 2^(n_rung-1) substeps of drift dt/2^(n_rung-1)
+    followed by the kick of the rungs due at that time.  Returns
+    (pos, mom, rung, state, rung_history)."""
+    pos = _f64(pos).copy()
+    mom = _f64(mom).copy()
+    acc, _ = sr_accel(pos, x_s, x_r, G_m, softening, eps, box=box)
+    rung, _ = rungs(acc, dt, eta, eps, n_rung)
+    state = np.zeros(pos.shape[1], dtype=np.int8)
+    mom = kick(mom, acc, [dt / 2.0 ** (l + 1) for l in range(n_rung)], rung=rung, rung_min=0)
+    sub = 2 ** (n_rung - 1)
+    history = []
+    k = 0
+    for step in range(n_steps):
+        for s in range(1, sub + 1):
+            k += 1
+            pos = drift(pos, mom, dt / sub, box)
+            tz = 0
+            while tz < n_rung - 1 and (k >> tz) & 1 == 0:
+                tz += 1
+            lmin = n_rung - 1 - tz
+            acc = np.zeros_like(pos)
+            acc, _ = sr_accel(pos, x_s, x_r, G_m, softening, eps, rung=rung, rung_min=lmin, box=box, out=acc)
+            sync = step == n_steps - 1 and s == sub
+            rung_kick(mom, acc, rung, state, lmin, k, n_rung, dt, eta, eps, sync)
+            history.append(rung.copy())
+    return pos, mom, rung, state, history

@@ -495,6 +495,56 @@ void oracle_drift(int64_t n, double* pos, const double* mom, double factor, doub
     }
 }
 
+/*
+ * One kick of the rung-based leapfrog (Section 2.2.2, time-stepping figure and
+ * text).  Rung-l momenta are kicked every dt/2^l; this kick happens at time
+ * k dt / 2^(n_rung-1) after the last synchronisation and touches the particles
+ * with rung >= rung_min.  A particle's kick is f dt / 2^l with f = 1 normally,
+ * 1/2 after a jump to a finer rung and 3/4 after a jump to a coarser one; with
+ * sync the kick stops at the synchronisation time (f - 1/2).  After a normal
+ * kick the rung of Eq. rung (oracle_rungs) decides: finer -> l+1 (next kick
+ * 1/2); coarser -> l-1 (next kick 3/4), but only when k dt/2^(n_rung-1) is an
+ * odd multiple of dt/2^l ("every other kick"); else unchanged.
+ * state: 0 (f = 1), 1 (f = 1/2), 2 (f = 3/4).  Returns non-finite count.
+ */
+int64_t oracle_rung_kick(int64_t n, double* mom, const double* acc, int8_t* rung, int8_t* state, int rung_min,
+                         long long k, int n_rung, double dt, double eta, double eps, int sync) {
+  double t1 = dt * dt;
+  double t2 = 2.0 * eta;
+  double t3 = t2 * eps;
+  double q = t1 / t3;
+  double qq = q * q;
+  int64_t bad = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int l = rung[i];
+    if (l < rung_min) continue;
+    double f = state[i] == 0 ? 1.0 : (state[i] == 1 ? 0.5 : 0.75);
+    double fac = sync ? f - 0.5 : f;
+    double K = ldexp(dt * fac, -l);
+    double a[3];
+    for (int d = 0; d < 3; ++d) {
+      a[d] = acc[d * n + i];
+      mom[d * n + i] = mom[d * n + i] + a[d] * K;
+    }
+    if (sync) { state[i] = 0; continue; }
+    double a2 = a[0] * a[0];
+    a2 = a2 + a[1] * a[1];
+    a2 = a2 + a[2] * a[2];
+    double s = qq * a2;
+    int lnew = 0;
+    if (!(s == s) || isinf(s)) {
+      ++bad;
+    } else {
+      double p = 1.0;
+      while (lnew < n_rung - 1 && s > p) { p *= 16.0; ++lnew; }
+    }
+    if (lnew > l) { rung[i] = (int8_t)(l + 1); state[i] = 1; }
+    else if (lnew < l && ((k >> (n_rung - 1 - l)) & 1LL)) { rung[i] = (int8_t)(l - 1); state[i] = 2; }
+    else state[i] = 0;
+  }
+  return bad;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

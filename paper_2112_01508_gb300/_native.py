@@ -34,6 +34,7 @@ EXPORTS = (
     "p3m_sr_create", "p3m_sr_destroy", "p3m_sr_last_error", "p3m_sr_sync", "p3m_sr_stats", "p3m_sr_sort",
     "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
     "p3m_sr_permute", "p3m_sr_unpermute", "p3m_sr_forces_noalloc", "p3m_sr_forces_tabulated",
+    "p3m_sr_rung_kick",
 )
 
 
@@ -123,6 +124,8 @@ def load() -> ctypes.CDLL:
         L.p3m_sr_forces_noalloc.restype = i
         L.p3m_sr_forces_tabulated.argtypes = [p, p, i, p]
         L.p3m_sr_forces_tabulated.restype = i
+        L.p3m_sr_rung_kick.argtypes = [p, p, i, p, i, p, p, i, ctypes.c_longlong, d, d, d, i]
+        L.p3m_sr_rung_kick.restype = i
         _lib = L
         return L
 
@@ -201,3 +204,10 @@ def p3m_sr_unpermute(ctx, src_ptr, dst_ptr, elem_bytes, rows) -> int:
 
 def p3m_sr_forces_tabulated(ctx, pos_ptr, table_bits, acc_ptr) -> int:
     return load().p3m_sr_forces_tabulated(ctx, ctypes.c_void_p(pos_ptr), int(table_bits), ctypes.c_void_p(acc_ptr))
+
+
+def p3m_sr_rung_kick(ctx, mom_ptr, mom_precision, acc_ptr, acc_precision, rung_ptr, state_ptr, rung_min, substep,
+                     dt, eta, eps, synchronize) -> int:
+    return load().p3m_sr_rung_kick(ctx, ctypes.c_void_p(mom_ptr), int(mom_precision), ctypes.c_void_p(acc_ptr),
+                                   int(acc_precision), ctypes.c_void_p(rung_ptr), ctypes.c_void_p(state_ptr),
+                                   int(rung_min), int(substep), float(dt), float(eta), float(eps), int(synchronize))

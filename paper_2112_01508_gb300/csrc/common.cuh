@@ -16,6 +16,7 @@ constexpr int kChunk = 32;  // receivers per chunk (one warp lane each)
 enum : int {
   kErrPosition = 1,      // non-finite or out-of-box position at binning
   kErrNonfiniteAcc = 2,  // non-finite acceleration at rung assignment
+  kErrRungState = 4,     // rung outside [0, n_rung) or kick state outside {0, 1, 2} at a rung kick
 };
 
 // Tile/subtile geometry of the periodic box (Section 2.1.3).

@@ -26,6 +26,8 @@ static p3m_status status_from_bits(p3m_sr_ctx* ctx, int bits) {
     return fail(ctx, P3M_ERR_NONFINITE, "a position was non-finite or outside [0, L) when binned");
   if (bits & kErrNonfiniteAcc)
     return fail(ctx, P3M_ERR_NONFINITE, "a non-finite acceleration was met by the rung assignment");
+  if (bits & kErrRungState)
+    return fail(ctx, P3M_ERR_STATE, "a rung kick met a rung outside [0, n_rung) or a kick state outside {0, 1, 2}");
   return P3M_OK;
 }
 

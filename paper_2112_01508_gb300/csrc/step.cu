@@ -74,6 +74,58 @@ __global__ void k_drift(double* __restrict__ pos, const M* __restrict__ mom, int
   }
 }
 
+// One kick of the rung-based leapfrog with the rung update (see p3m_sr_rung_kick).
+template <class M, class A>
+__global__ void k_rung_kick(M* __restrict__ mom, const A* __restrict__ acc, int8_t* __restrict__ rung,
+                            int8_t* __restrict__ state, int64_t n, int rung_min, long long k, int log2_sub, double dt,
+                            double qq, int n_rung, int sync, int* __restrict__ err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int l = rung[i];
+  if (l < rung_min) return;
+  const int st = state[i];
+  if (l >= n_rung || st < 0 || st > 2) {  // corrupted rung or state: leave the particle alone
+    atomicOr(err, kErrRungState);
+    return;
+  }
+  const double f = st == 0 ? 1.0 : (st == 1 ? 0.5 : 0.75);
+  const double fac = sync ? f - 0.5 : f;
+  const double K = ldexp(__dmul_rn(dt, fac), -l);  // fac dt / 2^l (the scaling is exact)
+  double a[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    a[d] = (double)acc[d * n + i];
+    mom[d * n + i] = (M)__dadd_rn((double)mom[d * n + i], __dmul_rn(a[d], K));
+  }
+  if (sync) {
+    state[i] = 0;
+    return;
+  }
+  // Eq. rung on the acceleration of this kick (same rule as k_rungs)
+  const double a2 = __dadd_rn(__dadd_rn(__dmul_rn(a[0], a[0]), __dmul_rn(a[1], a[1])), __dmul_rn(a[2], a[2]));
+  const double s = __dmul_rn(qq, a2);
+  int lnew = 0;
+  if (isnan(s) || isinf(s)) {
+    atomicOr(err, kErrNonfiniteAcc);
+  } else if (s > 1.0) {
+    long long b = __double_as_longlong(s);
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    int kk = e + (((b & 0xfffffffffffffLL) != 0) ? 1 : 0);
+    lnew = (kk + 3) >> 2;
+    if (lnew > n_rung - 1) lnew = n_rung - 1;
+  }
+  int out = l, ost = 0;
+  if (lnew > l) {
+    out = l + 1;  // next kick: half of the finer rung's usual kick
+    ost = 1;
+  } else if (lnew < l && ((k >> (log2_sub - l)) & 1LL)) {
+    out = l - 1;  // only at every other kick of rung l; next kick: 3/4 of the coarser rung's
+    ost = 2;
+  }
+  rung[i] = (int8_t)out;
+  state[i] = (int8_t)ost;
+}
+
 }  // namespace p3m
 
 using namespace p3m;
@@ -152,4 +204,52 @@ extern "C" p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom
   ctx->sorted = false;
   ctx->sorted_pos = nullptr;
   return cuda_check(ctx, cudaGetLastError(), "drift kernel");
+}
+
+extern "C" p3m_status p3m_sr_rung_kick(p3m_sr_ctx* ctx, void* mom, int mom_precision, const void* acc,
+                                       int acc_precision, int8_t* rung, int8_t* kick_state, int rung_min,
+                                       long long substep, double dt, double eta, double eps, int synchronize) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if ((mom_precision != 32 && mom_precision != 64) || (acc_precision != 32 && acc_precision != 64))
+    return fail(ctx, P3M_ERR_INVALID, "rung_kick: precision must be 32 or 64");
+  if (ctx->n > 0 && (!mom || !acc || !rung || !kick_state)) return fail(ctx, P3M_ERR_INVALID, "rung_kick: null pointer");
+  if (!(dt >= 0.0) || !(eta > 0.0) || !(eps > 0.0) || substep < 1)
+    return fail(ctx, P3M_ERR_INVALID, "rung_kick: need dt >= 0, eta > 0, eps > 0, substep >= 1");
+  const int log2_sub = ctx->prm.n_rung - 1;
+  const long long period = 1LL << log2_sub;
+  int tz = 0;
+  while (tz < log2_sub && ((substep >> tz) & 1LL) == 0) ++tz;
+  if (rung_min != log2_sub - tz) return fail(ctx, P3M_ERR_INVALID, "rung_kick: rung_min does not match the substep");
+  if (synchronize && (substep % period) != 0)
+    return fail(ctx, P3M_ERR_INVALID, "rung_kick: synchronisation only at the end of a global step");
+  p3m_status st = poll_latched(ctx);
+  if (st != P3M_OK) return st;
+  if (ctx->n == 0) return P3M_OK;
+  volatile double t1 = dt * dt;
+  volatile double t2 = 2.0 * eta;
+  volatile double t3 = t2 * eps;
+  volatile double q = t1 / t3;
+  const double qq = q * q;
+  const int t = 256;
+  const unsigned b = blocks_for(ctx->n, t);
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  const int nr = ctx->prm.n_rung;
+  const int sy = synchronize ? 1 : 0;
+  if (mom_precision == 64 && acc_precision == 32)
+    k_rung_kick<double, float><<<b, t, 0, s>>>((double*)mom, (const float*)acc, rung, kick_state, n, rung_min, substep,
+                                               log2_sub, dt, qq, nr, sy, ctx->err_dev);
+  else if (mom_precision == 64 && acc_precision == 64)
+    k_rung_kick<double, double><<<b, t, 0, s>>>((double*)mom, (const double*)acc, rung, kick_state, n, rung_min,
+                                                substep, log2_sub, dt, qq, nr, sy, ctx->err_dev);
+  else if (mom_precision == 32 && acc_precision == 32)
+    k_rung_kick<float, float><<<b, t, 0, s>>>((float*)mom, (const float*)acc, rung, kick_state, n, rung_min, substep,
+                                              log2_sub, dt, qq, nr, sy, ctx->err_dev);
+  else
+    k_rung_kick<float, double><<<b, t, 0, s>>>((float*)mom, (const double*)acc, rung, kick_state, n, rung_min,
+                                               substep, log2_sub, dt, qq, nr, sy, ctx->err_dev);
+  ++ctx->launches;
+  if ((st = cuda_check(ctx, cudaGetLastError(), "rung kick kernel")) != P3M_OK) return st;
+  report_latched(ctx);
+  return P3M_OK;
 }

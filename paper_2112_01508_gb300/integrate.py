@@ -1,0 +1,61 @@
+"""Rung-based leapfrog (Section 2.2.2) over the library's kernels.
+
+Every particle owns a rung l and is kicked every dt / 2^l; positions drift in
+2^(n_rung-1) substeps of dt / 2^(n_rung-1) per global step dt.  After each
+drift the particles are sorted again into tiles and subtiles (momenta, rungs,
+kick states and identifiers carried along), the receivers are the rungs due
+at that substep (all particles supply), and p3m_sr_rung_kick applies the kick
+with its rung jumps.  The run starts from a synchronised state with the
+paper's "fake kick" (forces of all particles, rungs from Eq. rung, half kicks
+dt / 2^(l+1)) and ends synchronised.  Only the short-range force is included
+(the long-range PM kick of rung 0 is outside this library).
+"""
+from __future__ import annotations
+
+import torch
+
+from .shortrange import ShortRange
+
+
+def substep_rung_min(k: int, n_rung: int) -> int:
+    """Lowest rung kicked at global substep k >= 1: n_rung - 1 - trailing zeros of k (>= 0)."""
+    tz = 0
+    while tz < n_rung - 1 and (k >> tz) & 1 == 0:
+        tz += 1
+    return n_rung - 1 - tz
+
+
+def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: float, eta: float, eps: float,
+                  n_steps: int, precision: int = 32, carry=(), history: list | None = None):
+    """Advance (pos, mom) by n_steps global steps of size dt.
+
+    pos (3, n) float64 and mom (3, n) float64/float32 are reordered in place by
+    the sorts; `carry` lists further per-particle tensors to reorder alongside
+    (for example identifiers).  Returns (rung, kick_state) in the final order.
+    """
+    n_rung = sr.n_rung
+    sub = 2 ** (n_rung - 1)
+    dev = pos.device
+    rung = torch.zeros(sr.n, dtype=torch.int8, device=dev)
+    state = torch.zeros(sr.n, dtype=torch.int8, device=dev)
+    carried = [mom, rung, state, *carry]
+    # fake kick: rungs from the forces of all particles, then half kicks per rung
+    sr.sort(pos, carry=carried)
+    sr.build_pairs()
+    acc = sr.forces(pos, precision)
+    sr.assign_rungs(acc, dt, eta, eps, rung)
+    sr.kick(mom, acc, [dt / 2.0 ** (l + 1) for l in range(n_rung)], rung, 0)
+    k = 0
+    for step in range(n_steps):
+        for s in range(1, sub + 1):
+            k += 1
+            sr.drift(pos, mom, dt / sub)
+            sr.sort(pos, carry=carried)
+            lmin = substep_rung_min(k, n_rung)
+            sr.build_pairs(rung, lmin)
+            sr.forces(pos, precision, acc)
+            sync = step == n_steps - 1 and s == sub
+            sr.rung_kick(mom, acc, rung, state, lmin, k, dt, eta, eps, synchronize=sync)
+            if history is not None:
+                history.append(rung.clone())
+    return rung, state

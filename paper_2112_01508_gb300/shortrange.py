@@ -171,6 +171,17 @@ class ShortRange:
         self._raise(nat.p3m_sr_kick(self._ctx, mom.data_ptr(), _PREC[mom.dtype], acc.data_ptr(), _PREC[acc.dtype],
                                     rung.data_ptr() if rung is not None else 0, rung_min, kf))
 
+    def rung_kick(self, mom: torch.Tensor, acc: torch.Tensor, rung: torch.Tensor, kick_state: torch.Tensor,
+                  rung_min: int, substep: int, dt: float, eta: float, eps: float, synchronize: bool = False):
+        """One kick of the rung-based leapfrog with rung jumps (p3m_sr_rung_kick)."""
+        _check(mom, "mom", (torch.float32, torch.float64), (3, self.n), self.device)
+        _check(acc, "acc", (torch.float32, torch.float64), (3, self.n), self.device)
+        _check(rung, "rung", torch.int8, (self.n,), self.device)
+        _check(kick_state, "kick_state", torch.int8, (self.n,), self.device)
+        self._raise(nat.p3m_sr_rung_kick(self._ctx, mom.data_ptr(), _PREC[mom.dtype], acc.data_ptr(), _PREC[acc.dtype],
+                                         rung.data_ptr(), kick_state.data_ptr(), rung_min, substep, dt, eta, eps,
+                                         int(synchronize)))
+
     def drift(self, pos: torch.Tensor, mom: torch.Tensor, factor: float):
         _check(pos, "pos", torch.float64, (3, self.n), self.device)
         _check(mom, "mom", (torch.float32, torch.float64), (3, self.n), self.device)

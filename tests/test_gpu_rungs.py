@@ -1,0 +1,93 @@
+"""GPU rung-based leapfrog (Section 2.2.2) against the oracle's cycle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2112_01508_gb300 import ShortRange
+from paper_2112_01508_gb300.integrate import rung_leapfrog, substep_rung_min
+
+pytestmark = pytest.mark.gpu
+
+W = synth.workload("n32k")
+
+
+def _subset(n, seed):
+    full = synth.workload_positions(W)
+    idx = np.random.default_rng(seed).choice(W.n, size=n, replace=False)
+    return np.ascontiguousarray(full[:, idx])
+
+
+def _dt_for_rungs(pos, eta, eps):
+    """A step for which the median particle sits on rung 1 of Eq. rung."""
+    acc, _ = oracle.sr_accel(pos, W.x_s, W.x_r, W.G_m, "bspline", eps)
+    a = np.sqrt((acc ** 2).sum(axis=0))
+    return 2.0 * float(np.sqrt(2 * eta * eps / np.median(a)))
+
+
+@pytest.mark.parametrize("n_rung,n_steps", [(4, 2), (3, 3)])
+def test_rung_leapfrog_vs_oracle(n_rung, n_steps):
+    n, eta, eps = 4096, 0.025, W.eps
+    pos = _subset(n, 5)
+    dt = _dt_for_rungs(pos, eta, eps)
+    p_ref, q_ref, rung_ref, state_ref, hist_ref = oracle.rung_leapfrog(
+        pos, np.zeros_like(pos), W.x_s, W.x_r, W.G_m, "bspline", eps, dt, eta, n_rung, n_steps)
+    # the run must exercise several rungs and jumps
+    assert len(np.unique(hist_ref[0])) >= 3
+    assert sum(int((a != b).sum()) for a, b in zip(hist_ref[:-1], hist_ref[1:])) > 0
+    dev = torch.device("cuda")
+    with ShortRange(n, W.x_s, W.x_r, W.G_m, softening="bspline", eps=eps, n_sub=W.n_sub, n_rung=n_rung) as sr:
+        p = torch.from_numpy(pos.copy()).to(dev)
+        q = torch.zeros_like(p)
+        ids = torch.arange(n, dtype=torch.int32, device=dev)
+        hist = []
+        rung, state = rung_leapfrog(sr, p, q, dt, eta, eps, n_steps, precision=64, carry=(ids,), history=hist)
+        sr.sync()
+        order = ids.cpu().numpy().astype(np.int64)
+        got_p = np.empty_like(pos)
+        got_q = np.empty_like(pos)
+        got_p[:, order] = p.cpu().numpy()
+        got_q[:, order] = q.cpu().numpy()
+        got_rung = np.empty(n, np.int8)
+        got_rung[order] = rung.cpu().numpy()
+        got_state = np.empty(n, np.int8)
+        got_state[order] = state.cpu().numpy()
+    np.testing.assert_array_equal(got_rung, rung_ref)
+    np.testing.assert_array_equal(got_state, state_ref)
+    assert np.all(got_state == 0)
+    # FP64 forces agree with the oracle to ~1e-13 relative; two to three steps keep that far below 1e-10
+    dp = got_p - p_ref
+    dp -= np.round(dp)  # periodic wrap
+    assert np.abs(dp).max() <= 1e-10 * W.x_r
+    assert np.abs(got_q - q_ref).max() <= 1e-10 * np.abs(q_ref).max()
+
+
+def test_substep_rung_min():
+    assert [substep_rung_min(k, 4) for k in range(1, 9)] == [3, 2, 3, 1, 3, 2, 3, 0]
+    assert [substep_rung_min(k, 1) for k in range(1, 4)] == [0, 0, 0]
+
+
+def test_rung_kick_rejects_bad_rung_and_order():
+    n = 256
+    dev = torch.device("cuda")
+    with ShortRange(n, W.x_s, W.x_r, W.G_m, softening="bspline", eps=W.eps, n_rung=4) as sr:
+        mom = torch.zeros((3, n), dtype=torch.float64, device=dev)
+        acc = torch.ones((3, n), dtype=torch.float64, device=dev)
+        rung = torch.zeros(n, dtype=torch.int8, device=dev)
+        state = torch.zeros(n, dtype=torch.int8, device=dev)
+        from paper_2112_01508_gb300 import _native as nat
+        # rung_min must match the substep counter
+        with pytest.raises(nat.P3MError) as e:
+            sr.rung_kick(mom, acc, rung, state, 2, 8, 0.1, 0.025, W.eps)
+        assert e.value.status == nat.P3M_ERR_INVALID
+        # synchronisation only at the end of a global step
+        with pytest.raises(nat.P3MError):
+            sr.rung_kick(mom, acc, rung, state, 3, 3, 0.1, 0.025, W.eps, synchronize=True)
+        rung[7] = 9
+        sr.rung_kick(mom, acc, rung, state, 0, 8, 0.1, 0.025, W.eps)
+        with pytest.raises(nat.P3MError) as e:
+            sr.sync()
+        assert e.value.status == nat.P3M_ERR_STATE
+        assert float(mom[:, 7].abs().max()) == 0.0
+        assert float(mom[:, 6].abs().min()) > 0.0

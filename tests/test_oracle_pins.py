@@ -376,3 +376,59 @@ def test_rejection_fractions(golden, case, offset):
     frac = rejected.mean()
     ref = golden["tile_pair_rejection_fraction"]
     assert abs(frac - ref[case]) <= ref["printed_precision"]
+
+
+# --------------------------------------------------------------------------
+# rung-based leapfrog (Section 2.2.2)
+# --------------------------------------------------------------------------
+
+def test_rung_kicks_give_total_impulse_a_dt():
+    """With a constant acceleration field, one synchronised global step kicks
+    every particle by exactly a * dt, whatever its rung and its rung jumps
+    (the kick sizes of the scheme always add up to the step)."""
+    n, n_rung = 2000, 4
+    dt, eta, eps = 0.1, 0.025, 0.01
+    rng = np.random.default_rng(3)
+    # accelerations spread over the rung ladder; initial rungs random, so that
+    # particles jump up and down during the step
+    mag = np.exp(rng.uniform(np.log(1e-2), np.log(1e4), n))
+    acc = rng.normal(size=(3, n))
+    acc *= mag / np.linalg.norm(acc, axis=0)
+    rung = rng.integers(0, n_rung, n).astype(np.int8)
+    state = np.zeros(n, dtype=np.int8)
+    mom = np.zeros((3, n))
+    mom = oracle.kick(mom, acc, [dt / 2.0 ** (l + 1) for l in range(n_rung)], rung=rung, rung_min=0)
+    sub = 2 ** (n_rung - 1)
+    jumps = 0
+    for k in range(1, sub + 1):
+        tz = 0
+        while tz < n_rung - 1 and (k >> tz) & 1 == 0:
+            tz += 1
+        before = rung.copy()
+        oracle.rung_kick(mom, acc, rung, state, n_rung - 1 - tz, k, n_rung, dt, eta, eps, sync=(k == sub))
+        jumps += int((before != rung).sum())
+    assert jumps > 100
+    np.testing.assert_allclose(mom, acc * dt, rtol=1e-13, atol=0)
+    assert np.all(state == 0)
+
+
+def test_rung_leapfrog_single_rung_is_plain_kdk():
+    """With one rung the scheme is the plain kick-drift-kick leapfrog."""
+    pos = _mixed_positions(1500, seed=4)
+    dt, eta = 0.02, 0.025
+    p1, q1, rung, state, _ = oracle.rung_leapfrog(pos, np.zeros_like(pos), XS, XR, GM, "bspline", EPS, dt, eta,
+                                                  n_rung=1, n_steps=3)
+    # kick-drift-kick with the inner half kicks merged into one kick of dt
+    x = pos.copy()
+    q = np.zeros_like(pos)
+    a, _ = oracle.sr_accel(x, XS, XR, GM, "bspline", EPS)
+    q = oracle.kick(q, a, [dt / 2])
+    for step in range(3):
+        x = oracle.drift(x, q, dt)
+        a, _ = oracle.sr_accel(x, XS, XR, GM, "bspline", EPS)
+        q = oracle.kick(q, a, [dt if step < 2 else dt / 2])
+    np.testing.assert_array_equal(p1, x)
+    np.testing.assert_array_equal(q1, q)
+    assert np.all(rung == 0)
+    # Newton III: all particles on one rung conserve the total momentum
+    assert np.abs(q1.sum(axis=1)).max() < 1e-12 * np.abs(q1).sum()
