@@ -314,6 +314,49 @@ def run_ours(args):
     tab_err = float(torch.sqrt(((acc_tab.double() - acc64) ** 2).sum() / (acc64 ** 2).sum()))
     tabulated = {"value": st.pairs_last / (statistics.mean(tab_ms) * 1e-3), "unit": UNIT,
                  "kernel_ms": statistics.mean(tab_ms), "rel_rms_vs_fp64": tab_err, "table_entries": 4096}
+    # substeps of the rung cycle on this state's rungs: receivers l >= l_cur (Section 2.2.2)
+    rung_substeps = {}
+    for lc in range(n_rung):
+        ts, tk = [], []
+        for _ in range(3):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sr.sort(pos, carry=[mom, rung])
+            sr.build_pairs(rung, lc)
+            sr.forces(pos, 32, acc)
+            sr.kick(mom, acc, [0.0] * n_rung, rung, lc)  # zero kick: timed, state unchanged
+            e1.record(stream)
+            st = sr.stats()
+            ts.append(e0.elapsed_time(e1))
+            tk.append(st.force_kernel_ms)
+        rung_substeps[str(lc)] = {"receivers": st.n_active, "pairs": st.pairs_last,
+                                  "substep_ms": statistics.mean(ts), "force_kernel_ms": statistics.mean(tk)}
+    # one global step of the full rung cycle (2^(n_rung-1) substeps, synchronised at its end)
+    from paper_2112_01508_gb300.integrate import rung_leapfrog
+    cyc = {}
+    for run in ("timed", "counted"):
+        pc, qc = pos0.clone(), torch.zeros_like(mom)
+        cyc_pairs = [0]
+
+        def count(k, lmin):
+            cyc_pairs[0] += sr.stats().pairs_last
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rung_leapfrog(sr, pc, qc, dt, eta, w.eps, 1, precision=32,
+                      on_substep=count if run == "counted" else None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cyc[run] = (e0.elapsed_time(e1), cyc_pairs[0])
+    del pc, qc
+    rung_cycle = {"value": cyc["counted"][1] / (cyc["timed"][0] * 1e-3), "unit": UNIT,
+                  "ms_per_global_step": cyc["timed"][0], "substeps": 2 ** (n_rung - 1),
+                  "pairs_per_global_step": cyc["counted"][1],
+                  "note": "fake kick + 128 substeps (drift, sort, work list, FP32 forces of due rungs, rung kick)"}
     # subtiles per tile (Section 2.1.3 "Subtiles"; the paper compares fixed 1^3 ... 9^3)
     sweep = {}
     pos_s = pos.clone()
@@ -375,6 +418,8 @@ def run_ours(args):
             "adjoint_over_forward": statistics.mean(vjp_ms) / statistics.mean(fwd_ms),
             "tabulated_2p12": tabulated,
             "n_sub_sweep_force_ms": sweep,
+            "rung_substeps": rung_substeps,
+            "rung_cycle": rung_cycle,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * 8 * n,

@@ -199,22 +199,31 @@ def rung_kick(mom, acc, rung, state, rung_min, substep, n_rung, dt, eta, eps, sy
                                     int(substep), int(n_rung), float(dt), float(eta), float(eps), int(bool(sync)))
 
 
-def rung_leapfrog(pos, mom, x_s, x_r, G_m, softening, eps, dt, eta, n_rung, n_steps, box=1.0):
-    """The rung-based KDK of Section 2.2.2 over n_steps global steps, synchronised
-    at the end: fake kick (forces of all particles, rungs of Eq. rung), half
-    kicks dt/2^(l+1) per rung, then 2^(n_rung-1) substeps of drift dt/2^(n_rung-1)
-    followed by the kick of the rungs due at that time.  Returns
-    (pos, mom, rung, state, rung_history)."""
+def rung_leapfrog(pos, mom, x_s, x_r, G_m, softening, eps, dt, eta, n_rung, n_steps, period=None, box=1.0):
+    """The rung-based KDK of Section 2.2.2 (the time-stepping figure) over
+    n_steps global steps of size dt, synchronised after every `period` steps
+    (default: once, at the end).
+
+    A period starts synchronised: rungs from Eq. rung on the forces of all
+    particles (the fake kick of the first period; the synchronising kick, in
+    which every particle is a receiver, for later ones), then the half kicks
+    dt/2^(l+1) per rung.  Each global step is 2^(n_rung-1) substeps of a drift
+    dt/2^(n_rung-1) followed by the kick of the rungs due at that time.
+    Returns (pos, mom, rung, state, rung_history)."""
     pos = _f64(pos).copy()
     mom = _f64(mom).copy()
+    period = n_steps if period is None else period
+    n = pos.shape[1]
     acc, _ = sr_accel(pos, x_s, x_r, G_m, softening, eps, box=box)
-    rung, _ = rungs(acc, dt, eta, eps, n_rung)
-    state = np.zeros(pos.shape[1], dtype=np.int8)
-    mom = kick(mom, acc, [dt / 2.0 ** (l + 1) for l in range(n_rung)], rung=rung, rung_min=0)
     sub = 2 ** (n_rung - 1)
     history = []
-    k = 0
     for step in range(n_steps):
+        if step % period == 0:
+            rung, _ = rungs(acc, dt, eta, eps, n_rung)
+            state = np.zeros(n, dtype=np.int8)
+            mom = kick(mom, acc, [dt / 2.0 ** (l + 1) for l in range(n_rung)], rung=rung, rung_min=0)
+            k = 0  # substeps since the synchronisation
+        last_of_period = (step + 1) % period == 0 or step == n_steps - 1
         for s in range(1, sub + 1):
             k += 1
             pos = drift(pos, mom, dt / sub, box)
@@ -222,9 +231,7 @@ def rung_leapfrog(pos, mom, x_s, x_r, G_m, softening, eps, dt, eta, n_rung, n_st
             while tz < n_rung - 1 and (k >> tz) & 1 == 0:
                 tz += 1
             lmin = n_rung - 1 - tz
-            acc = np.zeros_like(pos)
             acc, _ = sr_accel(pos, x_s, x_r, G_m, softening, eps, rung=rung, rung_min=lmin, box=box, out=acc)
-            sync = step == n_steps - 1 and s == sub
-            rung_kick(mom, acc, rung, state, lmin, k, n_rung, dt, eta, eps, sync)
+            rung_kick(mom, acc, rung, state, lmin, k, n_rung, dt, eta, eps, last_of_period and s == sub)
             history.append(rung.copy())
     return pos, mom, rung, state, history

@@ -26,27 +26,39 @@ def substep_rung_min(k: int, n_rung: int) -> int:
 
 
 def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: float, eta: float, eps: float,
-                  n_steps: int, precision: int = 32, carry=(), history: list | None = None):
-    """Advance (pos, mom) by n_steps global steps of size dt.
+                  n_steps: int, precision: int = 32, period: int | None = None, carry=(),
+                  history: list | None = None, on_substep=None):
+    """Advance (pos, mom) by n_steps global steps of size dt, synchronising after
+    every `period` steps (default: once, at the end).
 
-    pos (3, n) float64 and mom (3, n) float64/float32 are reordered in place by
-    the sorts; `carry` lists further per-particle tensors to reorder alongside
-    (for example identifiers).  Returns (rung, kick_state) in the final order.
+    A period starts synchronised: rungs from Eq. rung on the forces of all
+    particles (a fake kick for the first period; the synchronising kick, in
+    which every particle is a receiver, for later ones), then half kicks
+    dt / 2^(l+1).  pos (3, n) float64 and mom (3, n) float64/float32 are
+    reordered in place by the sorts; `carry` lists further per-particle
+    tensors to reorder alongside (for example identifiers).  `on_substep(k,
+    rung_min)` is called after each substep's kick is enqueued.  Returns
+    (rung, kick_state) in the final order.
     """
     n_rung = sr.n_rung
     sub = 2 ** (n_rung - 1)
+    period = n_steps if period is None else period
     dev = pos.device
     rung = torch.zeros(sr.n, dtype=torch.int8, device=dev)
     state = torch.zeros(sr.n, dtype=torch.int8, device=dev)
     carried = [mom, rung, state, *carry]
-    # fake kick: rungs from the forces of all particles, then half kicks per rung
     sr.sort(pos, carry=carried)
     sr.build_pairs()
     acc = sr.forces(pos, precision)
-    sr.assign_rungs(acc, dt, eta, eps, rung)
-    sr.kick(mom, acc, [dt / 2.0 ** (l + 1) for l in range(n_rung)], rung, 0)
+    half = [dt / 2.0 ** (l + 1) for l in range(n_rung)]
     k = 0
     for step in range(n_steps):
+        if step % period == 0:
+            sr.assign_rungs(acc, dt, eta, eps, rung)
+            state.zero_()
+            sr.kick(mom, acc, half, rung, 0)
+            k = 0  # substeps since the synchronisation
+        last_of_period = (step + 1) % period == 0 or step == n_steps - 1
         for s in range(1, sub + 1):
             k += 1
             sr.drift(pos, mom, dt / sub)
@@ -54,8 +66,9 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
             lmin = substep_rung_min(k, n_rung)
             sr.build_pairs(rung, lmin)
             sr.forces(pos, precision, acc)
-            sync = step == n_steps - 1 and s == sub
-            sr.rung_kick(mom, acc, rung, state, lmin, k, dt, eta, eps, synchronize=sync)
+            sr.rung_kick(mom, acc, rung, state, lmin, k, dt, eta, eps, synchronize=last_of_period and s == sub)
             if history is not None:
                 history.append(rung.clone())
+            if on_substep is not None:
+                on_substep(k, lmin)
     return rung, state

@@ -26,13 +26,13 @@ def _dt_for_rungs(pos, eta, eps):
     return 2.0 * float(np.sqrt(2 * eta * eps / np.median(a)))
 
 
-@pytest.mark.parametrize("n_rung,n_steps", [(4, 2), (3, 3)])
-def test_rung_leapfrog_vs_oracle(n_rung, n_steps):
+@pytest.mark.parametrize("n_rung,n_steps,period", [(4, 2, None), (3, 3, None), (4, 4, 2)])
+def test_rung_leapfrog_vs_oracle(n_rung, n_steps, period):
     n, eta, eps = 4096, 0.025, W.eps
     pos = _subset(n, 5)
     dt = _dt_for_rungs(pos, eta, eps)
     p_ref, q_ref, rung_ref, state_ref, hist_ref = oracle.rung_leapfrog(
-        pos, np.zeros_like(pos), W.x_s, W.x_r, W.G_m, "bspline", eps, dt, eta, n_rung, n_steps)
+        pos, np.zeros_like(pos), W.x_s, W.x_r, W.G_m, "bspline", eps, dt, eta, n_rung, n_steps, period=period)
     # the run must exercise several rungs and jumps
     assert len(np.unique(hist_ref[0])) >= 3
     assert sum(int((a != b).sum()) for a, b in zip(hist_ref[:-1], hist_ref[1:])) > 0
@@ -42,7 +42,8 @@ def test_rung_leapfrog_vs_oracle(n_rung, n_steps):
         q = torch.zeros_like(p)
         ids = torch.arange(n, dtype=torch.int32, device=dev)
         hist = []
-        rung, state = rung_leapfrog(sr, p, q, dt, eta, eps, n_steps, precision=64, carry=(ids,), history=hist)
+        rung, state = rung_leapfrog(sr, p, q, dt, eta, eps, n_steps, precision=64, period=period, carry=(ids,),
+                                    history=hist)
         sr.sync()
         order = ids.cpu().numpy().astype(np.int64)
         got_p = np.empty_like(pos)

@@ -432,3 +432,22 @@ def test_rung_leapfrog_single_rung_is_plain_kdk():
     assert np.all(rung == 0)
     # Newton III: all particles on one rung conserve the total momentum
     assert np.abs(q1.sum(axis=1)).max() < 1e-12 * np.abs(q1).sum()
+
+
+def test_rung_leapfrog_synchronised_every_step_is_unmerged_kdk():
+    """Synchronising after every step turns the one-rung scheme into kick
+    (dt/2) - drift (dt) - kick (dt/2) with nothing merged."""
+    pos = _mixed_positions(1500, seed=6)
+    dt, eta = 0.02, 0.025
+    p1, q1, _, _, _ = oracle.rung_leapfrog(pos, np.zeros_like(pos), XS, XR, GM, "bspline", EPS, dt, eta,
+                                           n_rung=1, n_steps=3, period=1)
+    x = pos.copy()
+    q = np.zeros_like(pos)
+    a, _ = oracle.sr_accel(x, XS, XR, GM, "bspline", EPS)
+    for step in range(3):
+        q = oracle.kick(q, a, [dt / 2])
+        x = oracle.drift(x, q, dt)
+        a, _ = oracle.sr_accel(x, XS, XR, GM, "bspline", EPS)
+        q = oracle.kick(q, a, [dt / 2])
+    np.testing.assert_array_equal(p1, x)
+    np.testing.assert_array_equal(q1, q)
