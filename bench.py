@@ -370,6 +370,19 @@ def run_ours(args):
                 s2.forces(pos_s, 32, acc_tab)
                 ts.append(s2.stats().force_kernel_ms)
             sweep[str(ns)] = statistics.mean(ts)
+    # temporal subtile refinement (trial of one more subdivision every 16 force calls)
+    from paper_2112_01508_gb300.refine import SubtileRefiner
+    with ShortRange.from_workload(w, device=dev, n_sub=1) as s2:
+        ref = SubtileRefiner(s2, interval=16, max_sub=4)
+        for _ in range(64):
+            ref.before_sort()
+            s2.sort(pos_s)
+            s2.build_pairs()
+            s2.forces(pos_s, 32, acc_tab)
+            ref.after_forces()
+        refinement = {"start_n_sub": 1, "final_n_sub": ref.current[0], "force_calls": 64, "interval": 16,
+                      "trials": [{"n_sub": e[1][0], "record_ps_per_pair": e[2] * 1e9,
+                                  "trial_ps_per_pair": e[3] * 1e9, "kept": e[4]} for e in ref.log.events]}
     del pos_s
 
     # end to end through the public API with host buffers
@@ -418,6 +431,7 @@ def run_ours(args):
             "adjoint_over_forward": statistics.mean(vjp_ms) / statistics.mean(fwd_ms),
             "tabulated_2p12": tabulated,
             "n_sub_sweep_force_ms": sweep,
+            "subtile_refinement": refinement,
             "rung_substeps": rung_substeps,
             "rung_cycle": rung_cycle,
             "roofline": roofline,

@@ -118,6 +118,19 @@ p3m_status p3m_sr_sync(p3m_sr_ctx* ctx);
 p3m_status p3m_sr_stats(p3m_sr_ctx* ctx, p3m_sr_stats_t* out);
 
 /*
+ * Change the subtile decomposition (Section 2.1.3, "Subtiles": the number of
+ * subtiles per tile is free, and the paper refines it while the simulation
+ * runs by timing a force computation with one more subdivision).
+ *   n_sub  HOST array of 3 ints in 1..16 (subtiles per tile per dimension).
+ * Forces do not depend on it beyond rounding.  The per-subtile arrays are
+ * reallocated when the subtile count grows (cudaFree/cudaMalloc, which wait for
+ * queued work; not inside stream capture).  The sort state is dropped: the
+ * next force, build_pairs or vjp call needs a p3m_sr_sort first
+ * (P3M_ERR_STATE).  On an error the old decomposition stays in force.
+ */
+p3m_status p3m_sr_set_subtiles(p3m_sr_ctx* ctx, const int* n_sub);
+
+/*
  * Sort the particles into tiles and subtiles (Section 2.1.3: O(N) sort into
  * tiles, memory reordered in tile -> subtile -> particle walk order).
  *   pos          3 x n float64 SoA, device; reordered IN PLACE.  Each position

@@ -34,7 +34,7 @@ EXPORTS = (
     "p3m_sr_create", "p3m_sr_destroy", "p3m_sr_last_error", "p3m_sr_sync", "p3m_sr_stats", "p3m_sr_sort",
     "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
     "p3m_sr_permute", "p3m_sr_unpermute", "p3m_sr_forces_noalloc", "p3m_sr_forces_tabulated",
-    "p3m_sr_rung_kick",
+    "p3m_sr_rung_kick", "p3m_sr_set_subtiles",
 )
 
 
@@ -126,6 +126,8 @@ def load() -> ctypes.CDLL:
         L.p3m_sr_forces_tabulated.restype = i
         L.p3m_sr_rung_kick.argtypes = [p, p, i, p, i, p, p, i, ctypes.c_longlong, d, d, d, i]
         L.p3m_sr_rung_kick.restype = i
+        L.p3m_sr_set_subtiles.argtypes = [p, ctypes.POINTER(i)]
+        L.p3m_sr_set_subtiles.restype = i
         _lib = L
         return L
 
@@ -154,6 +156,11 @@ def p3m_sr_stats(ctx):
     out = P3MStats()
     st = load().p3m_sr_stats(ctx, ctypes.byref(out))
     return st, out
+
+
+def p3m_sr_set_subtiles(ctx, n_sub) -> int:
+    arr = (ctypes.c_int * 3)(*[int(v) for v in n_sub])
+    return load().p3m_sr_set_subtiles(ctx, arr)
 
 
 def p3m_sr_sort(ctx, pos_ptr: int, carry_ptrs, carry_bytes, perm_out_ptr, subtile_id_out_ptr) -> int:

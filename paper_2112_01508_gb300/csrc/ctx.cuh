@@ -19,6 +19,7 @@ struct p3m_sr_ctx {
   int* keys[2] = {nullptr, nullptr};  // radix double buffers
   int* vals[2] = {nullptr, nullptr};
   int* offsets = nullptr;             // S + 1 (histogram, scanned in place)
+  int64_t offsets_cap = 0;            // allocated ints of offsets
   int* cell = nullptr;                // sorted subtile ids (aliases keys[k])
   int* perm = nullptr;                // sorted -> input index (aliases vals[k])
   int* hist = nullptr;                // radix digit histograms

@@ -223,6 +223,24 @@ void setup_force_consts(p3m_sr_ctx* ctx) {
   f.rsw2_d = (p.softening == 0) ? 0.0 : f.r_sw * f.r_sw;
 }
 
+// radix passes over ceil(log2(S)) key bits, at most 10 bits each
+static void setup_radix(p3m_sr_ctx* ctx) {
+  int key_bits = 1;
+  while (key_bits < 31 && ((int64_t)1 << key_bits) < ctx->geo.S) ++key_bits;
+  ctx->radix_passes = (key_bits + 9) / 10;
+  for (int k = 0, left = key_bits; k < ctx->radix_passes; ++k) {
+    int b = (left + (ctx->radix_passes - k) - 1) / (ctx->radix_passes - k);
+    ctx->radix_bits[k] = b;
+    left -= b;
+  }
+}
+
+// longest array the exclusive scan is applied to
+static int64_t scan_length(const p3m_sr_ctx* ctx) {
+  return std::max<int64_t>(std::max<int64_t>(ctx->geo.S + 1, ctx->n + 1),
+                           std::max<int64_t>(ctx->hist_ints, ctx->n_tiles + 1));
+}
+
 template <class T>
 static p3m_status alloc(p3m_sr_ctx* ctx, T** ptr, int64_t count, const char* what) {
   size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
@@ -261,19 +279,11 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
 
   const int64_t n = ctx->n;
   const int64_t S = ctx->geo.S;
-  // radix passes over ceil(log2(S)) key bits, at most 10 bits each
-  int key_bits = 1;
-  while (key_bits < 31 && ((int64_t)1 << key_bits) < S) ++key_bits;
-  ctx->radix_passes = (key_bits + 9) / 10;
-  for (int k = 0, left = key_bits; k < ctx->radix_passes; ++k) {
-    int b = (left + (ctx->radix_passes - k) - 1) / (ctx->radix_passes - k);
-    ctx->radix_bits[k] = b;
-    left -= b;
-  }
+  setup_radix(ctx);
   int64_t radix_blocks = (n + 4095) / 4096;
   ctx->hist_ints = 1024 * (radix_blocks > 0 ? radix_blocks : 1);
-  int64_t scan_n = std::max<int64_t>(std::max<int64_t>(S + 1, n + 1), std::max<int64_t>(ctx->hist_ints, ctx->n_tiles + 1));
-  ctx->scan_scratch_ints = scan_scratch_ints(scan_n);
+  ctx->scan_scratch_ints = scan_scratch_ints(scan_length(ctx));
+  ctx->offsets_cap = S + 1;
   ctx->max_chunks = std::min<int64_t>(n, ctx->n_tiles) + (n + kChunk - 1) / kChunk + 1;
 
 #define P3M_ALLOC(ptr, count) \
@@ -326,6 +336,52 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
   return P3M_OK;
 fail_alloc:
   p3m_sr_destroy(ctx);
+  return st;
+}
+
+extern "C" p3m_status p3m_sr_set_subtiles(p3m_sr_ctx* ctx, const int* n_sub) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (!n_sub) return fail(ctx, P3M_ERR_INVALID, "set_subtiles: null n_sub");
+  p3m_sr_params p = ctx->prm;
+  for (int d = 0; d < 3; ++d) p.n_sub[d] = n_sub[d];
+  p3m_status st = validate_params(ctx, p);
+  if (st != P3M_OK) return st;
+  int64_t S = (int64_t)std::floor(p.box / p.x_r);
+  S = S * p.n_sub[0] * S * p.n_sub[1] * S * p.n_sub[2];
+  if (S > 0x7fffffffLL - 2) return fail(ctx, P3M_ERR_INVALID, "set_subtiles: too many subtiles");
+  if ((st = poll_latched(ctx)) != P3M_OK) return st;
+  const p3m_sr_params old_prm = ctx->prm;
+  const Geometry old_geo = ctx->geo;
+  ctx->prm = p;
+  setup_geometry(ctx);
+  // per-subtile offsets and the scan scratch grow with S; cudaFree waits for queued work
+  int64_t scan_ints = scan_scratch_ints(scan_length(ctx));
+  int* new_offsets = nullptr;
+  int* new_scan = nullptr;
+  if (S + 1 > ctx->offsets_cap && (st = alloc(ctx, &new_offsets, S + 1, "offsets")) != P3M_OK) goto restore;
+  if (scan_ints > ctx->scan_scratch_ints && (st = alloc(ctx, &new_scan, scan_ints, "scan_scratch")) != P3M_OK) {
+    cudaFree(new_offsets);
+    goto restore;
+  }
+  if (new_offsets) {
+    cudaFree(ctx->offsets);
+    ctx->offsets = new_offsets;
+    ctx->offsets_cap = S + 1;
+  }
+  if (new_scan) {
+    cudaFree(ctx->scan_scratch);
+    ctx->scan_scratch = new_scan;
+    ctx->scan_scratch_ints = scan_ints;
+  }
+  setup_radix(ctx);
+  ctx->sorted = false;
+  ctx->sorted_pos = nullptr;
+  ctx->pairs_built = false;
+  ctx->all_chunks_built = false;
+  return P3M_OK;
+restore:
+  ctx->prm = old_prm;
+  ctx->geo = old_geo;
   return st;
 }
 

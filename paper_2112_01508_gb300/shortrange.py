@@ -62,6 +62,7 @@ class ShortRange:
         self.params = p
         self.n = int(n)
         self.n_rung = int(n_rung)
+        self.n_sub = ns
         with torch.cuda.device(self.device):
             st, ctx = nat.p3m_sr_create(p, self.stream.cuda_stream)
         if st != nat.P3M_OK:
@@ -98,6 +99,12 @@ class ShortRange:
             raise nat.P3MError(st, nat.p3m_sr_last_error(self._ctx))
 
     # -- entry points ------------------------------------------------------------
+    def set_subtiles(self, n_sub):
+        """Change the subtiles per tile (p3m_sr_set_subtiles); sort again before the next force call."""
+        ns = (n_sub,) * 3 if isinstance(n_sub, int) else tuple(int(v) for v in n_sub)
+        self._raise(nat.p3m_sr_set_subtiles(self._ctx, ns))
+        self.n_sub = ns
+
     def sort(self, pos: torch.Tensor, carry=(), perm_out: torch.Tensor | None = None,
              subtile_id_out: torch.Tensor | None = None):
         """Sort in place into tile -> subtile walk order (p3m_sr_sort)."""
