@@ -14,6 +14,9 @@ Parity pins (each checked by a ``-m "not gpu"`` test):
   * Newton's third law, permutation and translation invariance;
   * VJP against central finite differences of the oracle's own forward;
   * rungs against the log2/ceil definition; subtile ids against floor().
+
+The long-range (particle-mesh) half of Eq. p3m_gravity is restated in
+``oracle/pm.py`` (numpy, FP64) with its own pins.
 """
 from __future__ import annotations
 
