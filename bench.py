@@ -314,6 +314,39 @@ def run_ours(args):
     tab_err = float(torch.sqrt(((acc_tab.double() - acc64) ** 2).sum() / (acc64 ** 2).sum()))
     tabulated = {"value": st.pairs_last / (statistics.mean(tab_ms) * 1e-3), "unit": UNIT,
                  "kernel_ms": statistics.mean(tab_ms), "rel_rms_vs_fp64": tab_err, "table_entries": 4096}
+    # long-range half of the P3M force on the mesh of Eq. phi_gridsize_preference (n_phi = 2 cbrt N)
+    from paper_2112_01508_gb300 import LongRange
+    long_range = {}
+    for prec in (32, 64):
+        with LongRange.from_workload(w, precision=prec, device=dev) as lr:
+            out = torch.empty((3, n), dtype=torch.float32 if prec == 32 else torch.float64, device=dev)
+            for _ in range(2):
+                lr.accel(pos, out)
+            ts, phases = [], []
+            for _ in range(5):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lr.accel(pos, out)
+                e1.record(stream)
+                st_pm = lr.stats()
+                ts.append(e0.elapsed_time(e1))
+                phases.append(st_pm)
+            if prec == 64:
+                lr64 = out.clone()
+            else:
+                lr32 = out.clone()
+            long_range[f"fp{prec}"] = {
+                "ms": statistics.mean(ts), "n_phi": st_pm.n_phi, "p_i": 2, "p_d": 4,
+                "assign_ms": statistics.mean(x.assign_ms for x in phases),
+                "fft_ms": statistics.mean(x.fft_ms for x in phases),
+                "green_ms": statistics.mean(x.kernel_ms for x in phases),
+                "ifft_ms": statistics.mean(x.ifft_ms for x in phases),
+                "interp_ms": statistics.mean(x.interp_ms for x in phases),
+                "mesh_bytes": st_pm.mesh_bytes, "fft_work_bytes": st_pm.fft_work_bytes}
+    long_range["fp32_vs_fp64_rel_rms"] = float(torch.sqrt(((lr32.double() - lr64) ** 2).sum() / (lr64 ** 2).sum()))
+    del lr32, lr64
     # substeps of the rung cycle on this state's rungs: receivers l >= l_cur (Section 2.2.2)
     rung_substeps = {}
     for lc in range(n_rung):
@@ -431,6 +464,7 @@ def run_ours(args):
             "adjoint_over_forward": statistics.mean(vjp_ms) / statistics.mean(fwd_ms),
             "tabulated_2p12": tabulated,
             "n_sub_sweep_force_ms": sweep,
+            "long_range_pm": long_range,
             "subtile_refinement": refinement,
             "rung_substeps": rung_substeps,
             "rung_cycle": rung_cycle,

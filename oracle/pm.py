@@ -56,7 +56,12 @@ def _stencil(pos, n_phi: int, p_i: int, box: float):
     base = np.floor(s).astype(np.int64)
     offs = np.arange(-2, 4)
     cells = base[:, :, None] + offs[None, None, :]          # (3, n, 6)
-    w = weight_1d(cells - s[:, :, None], p_i)               # W((x_m - x_j)/L_phi), W even
+    if p_i == 1:
+        # NGP: the cell holding x.  Eq. W_NGP's strict |x| < 1/2 leaves a particle exactly
+        # on a cell face with no cell; it goes to the upper one, floor(s + 1/2).
+        w = (cells == np.floor(s + 0.5).astype(np.int64)[:, :, None]).astype(np.float64)
+    else:
+        w = weight_1d(cells - s[:, :, None], p_i)           # W((x_m - x_j)/L_phi), W even
     return np.mod(cells, n_phi), w
 
 

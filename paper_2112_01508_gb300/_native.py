@@ -218,3 +218,116 @@ def p3m_sr_rung_kick(ctx, mom_ptr, mom_precision, acc_ptr, acc_precision, rung_p
     return load().p3m_sr_rung_kick(ctx, ctypes.c_void_p(mom_ptr), int(mom_precision), ctypes.c_void_p(acc_ptr),
                                    int(acc_precision), ctypes.c_void_p(rung_ptr), ctypes.c_void_p(state_ptr),
                                    int(rung_min), int(substep), float(dt), float(eta), float(eps), int(synchronize))
+
+
+# ---- the long-range mesh library (include/p3m_pm.h) -----------------------------
+
+from .buildlib import LIB_PM  # noqa: E402
+
+# Every symbol declared in include/p3m_pm.h.
+PM_EXPORTS = (
+    "p3m_pm_create", "p3m_pm_destroy", "p3m_pm_last_error", "p3m_pm_sync", "p3m_pm_stats", "p3m_pm_accel",
+    "p3m_pm_assign", "p3m_pm_potential",
+)
+
+
+class PMParams(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("box", ctypes.c_double),
+        ("n_phi", ctypes.c_int),
+        ("x_s", ctypes.c_double),
+        ("G_m", ctypes.c_double),
+        ("p_i", ctypes.c_int),
+        ("p_d", ctypes.c_int),
+        ("precision", ctypes.c_int),
+    ]
+
+
+class PMStats(ctypes.Structure):
+    _fields_ = [
+        ("n_phi", ctypes.c_int),
+        ("mesh_bytes", ctypes.c_int64),
+        ("fft_work_bytes", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+        ("assign_ms", ctypes.c_double),
+        ("fft_ms", ctypes.c_double),
+        ("kernel_ms", ctypes.c_double),
+        ("ifft_ms", ctypes.c_double),
+        ("interp_ms", ctypes.c_double),
+    ]
+
+
+_pm = None
+
+
+def pm_lib_path() -> str:
+    return LIB_PM
+
+
+def load_pm() -> ctypes.CDLL:
+    """Load libp3m_pm.so; raises if it has not been built."""
+    global _pm
+    with _lock:
+        if _pm is not None:
+            return _pm
+        if not os.path.exists(LIB_PM):
+            raise ImportError(
+                f"{LIB_PM} is missing: build the CUDA libraries first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PM)
+        p, i = ctypes.c_void_p, ctypes.c_int
+        L.p3m_pm_create.argtypes = [ctypes.POINTER(PMParams), p, ctypes.POINTER(p)]
+        L.p3m_pm_create.restype = i
+        L.p3m_pm_destroy.argtypes = [p]
+        L.p3m_pm_destroy.restype = None
+        L.p3m_pm_last_error.argtypes = [p]
+        L.p3m_pm_last_error.restype = ctypes.c_char_p
+        L.p3m_pm_sync.argtypes = [p]
+        L.p3m_pm_sync.restype = i
+        L.p3m_pm_stats.argtypes = [p, ctypes.POINTER(PMStats)]
+        L.p3m_pm_stats.restype = i
+        L.p3m_pm_accel.argtypes = [p, p, p, i]
+        L.p3m_pm_accel.restype = i
+        L.p3m_pm_assign.argtypes = [p, p, p]
+        L.p3m_pm_assign.restype = i
+        L.p3m_pm_potential.argtypes = [p, p]
+        L.p3m_pm_potential.restype = i
+        _pm = L
+        return L
+
+
+def p3m_pm_create(params: PMParams, cuda_stream: int):
+    ctx = ctypes.c_void_p()
+    st = load_pm().p3m_pm_create(ctypes.byref(params), ctypes.c_void_p(cuda_stream), ctypes.byref(ctx))
+    return st, ctx
+
+
+def p3m_pm_destroy(ctx) -> None:
+    load_pm().p3m_pm_destroy(ctx)
+
+
+def p3m_pm_last_error(ctx) -> str:
+    return load_pm().p3m_pm_last_error(ctx).decode(errors="replace")
+
+
+def p3m_pm_sync(ctx) -> int:
+    return load_pm().p3m_pm_sync(ctx)
+
+
+def p3m_pm_stats(ctx):
+    out = PMStats()
+    st = load_pm().p3m_pm_stats(ctx, ctypes.byref(out))
+    return st, out
+
+
+def p3m_pm_accel(ctx, pos_ptr: int, acc_ptr: int, accumulate: int) -> int:
+    return load_pm().p3m_pm_accel(ctx, ctypes.c_void_p(pos_ptr), ctypes.c_void_p(acc_ptr), int(accumulate))
+
+
+def p3m_pm_assign(ctx, pos_ptr: int, rho_ptr: int) -> int:
+    return load_pm().p3m_pm_assign(ctx, ctypes.c_void_p(pos_ptr), ctypes.c_void_p(rho_ptr))
+
+
+def p3m_pm_potential(ctx, phi_ptr: int) -> int:
+    return load_pm().p3m_pm_potential(ctx, ctypes.c_void_p(phi_ptr))

@@ -1,8 +1,9 @@
-"""Build the CUDA library (sm_103a) in-tree.
+"""Build the CUDA libraries (sm_103a) in-tree.
 
 ``build()`` compiles every ``csrc/*.cu`` translation unit with nvcc in
-parallel and links ``libp3m_sr.so`` next to this file.  Objects go to
-``_build/`` (git-ignored).  Rebuilds only what changed.
+parallel and links ``libp3m_sr.so`` (short-range path) next to this file, and
+``csrc/pm/*.cu`` into ``libp3m_pm.so`` (long-range mesh path, linked against
+cuFFT).  Objects go to ``_build/`` (git-ignored).  Rebuilds only what changed.
 """
 from __future__ import annotations
 
@@ -16,6 +17,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libp3m_sr.so")
+LIB_PM = os.path.join(HERE, "libp3m_pm.so")
+CUDA_LIB = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(shutil.which("nvcc") or
+                                                                         "/usr/local/cuda/bin/nvcc"))), "lib64")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                      "-I" + os.path.join(HERE, "..", "include")]
@@ -42,11 +46,8 @@ def _compile(src: str, obj: str, extra: list[str]) -> None:
     os.replace(obj + ".tmp", obj)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile csrc/*.cu for sm_103a and link libp3m_sr.so.  Returns the library path."""
+def _build_one(srcs: list[str], lib: str, link_extra: list[str], force: bool, extra: list[str]) -> None:
     os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra_flags or [])
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_t = _headers_mtime()
     jobs = []
     objs = []
@@ -60,15 +61,29 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             futs = [ex.submit(_compile, s, o, extra) for s, o in jobs]
             for f in futs:
                 f.result()
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
+    if jobs or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"] + link_extra
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
+    """Compile csrc/*.cu and csrc/pm/*.cu for sm_103a and link libp3m_sr.so and
+    libp3m_pm.so.  Returns the short-range library's path."""
+    extra = list(extra_flags or [])
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    pm_srcs = sorted(glob.glob(os.path.join(CSRC, "pm", "*.cu")))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=2) as ex:
+        a = ex.submit(_build_one, srcs, LIB, [], force, extra)
+        b = ex.submit(_build_one, pm_srcs, LIB_PM, ["-L" + CUDA_LIB, "-lcufft", "-Xlinker", "-rpath=" + CUDA_LIB],
+                      force, extra)
+        a.result()
+        b.result()
     if verbose:
-        print("built", LIB)
+        print("built", LIB, "and", LIB_PM)
     return LIB
 
 

@@ -12,9 +12,9 @@ from paper_2112_01508_gb300 import _native as nat
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared_functions():
+def _declared_functions(header="*.h"):
     names = set()
-    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+    for h in glob.glob(os.path.join(ROOT, "include", header)):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         names |= set(re.findall(r"\b(p3m_\w+)\s*\(", text))
@@ -23,11 +23,39 @@ def _declared_functions():
 
 def test_library_exports_every_declared_symbol():
     lib = nat.load()
-    declared = _declared_functions()
+    declared = _declared_functions("p3m_sr.h")
     assert declared, "no declarations found"
     missing = [s for s in declared if not hasattr(lib, s)]
     assert not missing, missing
     assert set(nat.EXPORTS) == declared
+
+
+def test_mesh_library_exports_every_declared_symbol():
+    lib = nat.load_pm()
+    declared = _declared_functions("p3m_pm.h")
+    assert declared, "no declarations found"
+    missing = [s for s in declared if not hasattr(lib, s)]
+    assert not missing, missing
+    assert set(nat.PM_EXPORTS) == declared
+    assert _declared_functions() == declared | set(nat.EXPORTS)
+
+
+def _pm_params(**kw):
+    p = nat.PMParams()
+    p.n, p.box, p.n_phi, p.x_s, p.G_m, p.p_i, p.p_d, p.precision = 1000, 1.0, 64, 1.25 / 64, 1e-3, 2, 4, 32
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("kw", [dict(n=-1), dict(box=0.0), dict(n_phi=7), dict(n_phi=6), dict(n_phi=8192),
+                                dict(x_s=-0.1), dict(p_i=0), dict(p_i=5), dict(p_d=3), dict(p_d=10),
+                                dict(precision=16), dict(G_m=float("inf"))])
+def test_mesh_create_rejects_bad_parameters(kw):
+    # validation happens before any device call, so this runs without a GPU
+    st, ctx = nat.p3m_pm_create(_pm_params(**kw), 0)
+    assert st == nat.P3M_ERR_INVALID
+    assert not ctx.value
 
 
 def _params(**kw):

@@ -170,3 +170,27 @@ def test_pm_poisson_kernel_two_particles_attract():
     assert a[0, 0] == pytest.approx(-a[0, 1], rel=1e-12)
     ew = oracle.sr_accel(pos, 0.02, 0.25, 0.5, "none", 0.0)[0] + pm.ewald_lr_exact(pos, 0.02, 0.5)
     assert a[0, 0] == pytest.approx(ew[0, 0], rel=0.03)
+
+
+def test_ngp_particle_on_a_cell_face_goes_to_the_upper_cell():
+    # reading of Eq. W_NGP's strict inequality: the cell holding x is floor(x / L_phi)
+    pos = np.array([[4.0 / 16], [0.5 / 16], [0.5 / 16]])
+    rho = pm.assign(pos, 16, 1)
+    assert rho.sum() == 1.0 and rho[4, 0, 0] == 1.0
+
+
+def test_p3m_split_reproduces_the_periodic_force():
+    """The two halves of Eq. p3m_gravity together (oracle short-range sum cut at
+    x_r = 4.5 x_s, mesh long-range force at x_s = 1.25 L_phi with CIC and D_4)
+    give the full periodic force of an Ewald sum to a few tenths of a percent."""
+    rng = np.random.default_rng(8)
+    n = 128
+    pos = rng.random((3, n))
+    n_phi = 32
+    x_s = 1.25 / n_phi
+    sr, _ = oracle.sr_accel(pos, x_s, 4.5 * x_s, 1.0 / n, "none", 0.0)
+    lr = pm.lr_accel(pos, n_phi, x_s, 1.0 / n)
+    exact = oracle.sr_accel(pos, 0.02, 0.25, 1.0 / n, "none", 0.0)[0] + pm.ewald_lr_exact(pos, 0.02, 1.0 / n)
+    assert _rel_rms(sr + lr, exact) <= 5e-3
+    # each half alone is far off: the split really is a split
+    assert _rel_rms(sr, exact) > 0.05 and _rel_rms(lr, exact) > 0.05
