@@ -74,7 +74,8 @@ def test_momentum_conservation_and_accumulate(n32k):
         out = base.clone()
         lr.accel(p, out, accumulate=True)
         lr.sync()
-        torch.testing.assert_close(out, base + a, rtol=0, atol=1e-15 * float(a.abs().max()) + 1e-300)
+        # the second call's atomics may sum the mesh in another order: compare to rounding
+        torch.testing.assert_close(out, base + a, rtol=1e-14, atol=1e-12 * float(a.abs().max()))
 
 
 def test_ragged_and_empty_sets():
