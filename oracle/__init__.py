@@ -202,7 +202,8 @@ def rung_kick(mom, acc, rung, state, rung_min, substep, n_rung, dt, eta, eps, sy
                                     int(substep), int(n_rung), float(dt), float(eta), float(eps), int(bool(sync)))
 
 
-def rung_leapfrog(pos, mom, x_s, x_r, G_m, softening, eps, dt, eta, n_rung, n_steps, period=None, box=1.0):
+def rung_leapfrog(pos, mom, x_s, x_r, G_m, softening, eps, dt, eta, n_rung, n_steps, period=None, box=1.0,
+                  n_phi=None, p_i=2, p_d=4):
     """The rung-based KDK of Section 2.2.2 (the time-stepping figure) over
     n_steps global steps of size dt, synchronised after every `period` steps
     (default: once, at the end).
@@ -212,7 +213,11 @@ def rung_leapfrog(pos, mom, x_s, x_r, G_m, softening, eps, dt, eta, n_rung, n_st
     which every particle is a receiver, for later ones), then the half kicks
     dt/2^(l+1) per rung.  Each global step is 2^(n_rung-1) substeps of a drift
     dt/2^(n_rung-1) followed by the kick of the rungs due at that time.
-    Returns (pos, mom, rung, state, rung_history)."""
+    With n_phi given, the long-range mesh force (oracle.pm, orders p_i, p_d) kicks
+    every particle whenever rung 0 is kicked: dt/2 at the start of a period, dt at
+    the end of each global step (dt/2 at a synchronisation), after the short-range
+    kick.  Returns (pos, mom, rung, state, rung_history)."""
+    from . import pm as _pm
     pos = _f64(pos).copy()
     mom = _f64(mom).copy()
     period = n_steps if period is None else period
@@ -225,6 +230,8 @@ def rung_leapfrog(pos, mom, x_s, x_r, G_m, softening, eps, dt, eta, n_rung, n_st
             rung, _ = rungs(acc, dt, eta, eps, n_rung)
             state = np.zeros(n, dtype=np.int8)
             mom = kick(mom, acc, [dt / 2.0 ** (l + 1) for l in range(n_rung)], rung=rung, rung_min=0)
+            if n_phi:
+                mom = kick(mom, _pm.lr_accel(pos, n_phi, x_s, G_m, p_i, p_d, box), [dt / 2.0])
             k = 0  # substeps since the synchronisation
         last_of_period = (step + 1) % period == 0 or step == n_steps - 1
         for s in range(1, sub + 1):
@@ -236,5 +243,8 @@ def rung_leapfrog(pos, mom, x_s, x_r, G_m, softening, eps, dt, eta, n_rung, n_st
             lmin = n_rung - 1 - tz
             acc, _ = sr_accel(pos, x_s, x_r, G_m, softening, eps, rung=rung, rung_min=lmin, box=box, out=acc)
             rung_kick(mom, acc, rung, state, lmin, k, n_rung, dt, eta, eps, last_of_period and s == sub)
+            if n_phi and s == sub:
+                kf = dt / 2.0 if last_of_period else dt
+                mom = kick(mom, _pm.lr_accel(pos, n_phi, x_s, G_m, p_i, p_d, box), [kf])
             history.append(rung.copy())
     return pos, mom, rung, state, history

@@ -7,8 +7,12 @@ kick states and identifiers carried along), the receivers are the rungs due
 at that substep (all particles supply), and p3m_sr_rung_kick applies the kick
 with its rung jumps.  The run starts from a synchronised state with the
 paper's "fake kick" (forces of all particles, rungs from Eq. rung, half kicks
-dt / 2^(l+1)) and ends synchronised.  Only the short-range force is included
-(the long-range PM kick of rung 0 is outside this library).
+dt / 2^(l+1)) and ends synchronised.
+
+With a ``LongRange`` context the mesh force kicks every particle whenever
+rung 0 is kicked (the paper's rule): dt/2 at the start of a period, dt at the
+end of each global step, dt/2 at a synchronisation, after the short-range
+kick.  Rungs follow the short-range force alone, as in the paper.
 """
 from __future__ import annotations
 
@@ -27,7 +31,7 @@ def substep_rung_min(k: int, n_rung: int) -> int:
 
 def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: float, eta: float, eps: float,
                   n_steps: int, precision: int = 32, period: int | None = None, carry=(),
-                  history: list | None = None, on_substep=None):
+                  history: list | None = None, on_substep=None, long_range=None):
     """Advance (pos, mom) by n_steps global steps of size dt, synchronising after
     every `period` steps (default: once, at the end).
 
@@ -50,6 +54,7 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
     sr.sort(pos, carry=carried)
     sr.build_pairs()
     acc = sr.forces(pos, precision)
+    acc_lr = None if long_range is None else torch.empty((3, sr.n), dtype=long_range.dtype, device=dev)
     half = [dt / 2.0 ** (l + 1) for l in range(n_rung)]
     k = 0
     for step in range(n_steps):
@@ -57,6 +62,9 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
             sr.assign_rungs(acc, dt, eta, eps, rung)
             state.zero_()
             sr.kick(mom, acc, half, rung, 0)
+            if long_range is not None:
+                long_range.accel(pos, acc_lr)
+                sr.kick(mom, acc_lr, [dt / 2.0])
             k = 0  # substeps since the synchronisation
         last_of_period = (step + 1) % period == 0 or step == n_steps - 1
         for s in range(1, sub + 1):
@@ -67,6 +75,9 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
             sr.build_pairs(rung, lmin)
             sr.forces(pos, precision, acc)
             sr.rung_kick(mom, acc, rung, state, lmin, k, dt, eta, eps, synchronize=last_of_period and s == sub)
+            if long_range is not None and s == sub:
+                long_range.accel(pos, acc_lr)
+                sr.kick(mom, acc_lr, [dt / 2.0 if last_of_period else dt])
             if history is not None:
                 history.append(rung.clone())
             if on_substep is not None:

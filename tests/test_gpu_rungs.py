@@ -92,3 +92,34 @@ def test_rung_kick_rejects_bad_rung_and_order():
         assert e.value.status == nat.P3M_ERR_STATE
         assert float(mom[:, 7].abs().max()) == 0.0
         assert float(mom[:, 6].abs().min()) > 0.0
+
+
+def test_rung_leapfrog_with_long_range_vs_oracle():
+    """The full P3M cycle: short-range rung kicks plus the mesh force on every rung-0 kick."""
+    from paper_2112_01508_gb300 import LongRange
+    n, eta, eps, n_rung, n_steps, n_phi = 4096, 0.025, W.eps, 3, 2, 32
+    pos = _subset(n, 7)
+    dt = _dt_for_rungs(pos, eta, eps)
+    p_ref, q_ref, rung_ref, _, _ = oracle.rung_leapfrog(
+        pos, np.zeros_like(pos), W.x_s, W.x_r, W.G_m, "bspline", eps, dt, eta, n_rung, n_steps, n_phi=n_phi)
+    dev = torch.device("cuda")
+    with ShortRange(n, W.x_s, W.x_r, W.G_m, softening="bspline", eps=eps, n_sub=W.n_sub, n_rung=n_rung) as sr, \
+            LongRange(n, n_phi, W.x_s, W.G_m, precision=64) as lr:
+        p = torch.from_numpy(pos.copy()).to(dev)
+        q = torch.zeros_like(p)
+        ids = torch.arange(n, dtype=torch.int32, device=dev)
+        rung, _ = rung_leapfrog(sr, p, q, dt, eta, eps, n_steps, precision=64, carry=(ids,), long_range=lr)
+        sr.sync()
+        lr.sync()
+        order = ids.cpu().numpy().astype(np.int64)
+        got_p = np.empty_like(pos)
+        got_q = np.empty_like(pos)
+        got_p[:, order] = p.cpu().numpy()
+        got_q[:, order] = q.cpu().numpy()
+        got_rung = np.empty(n, np.int8)
+        got_rung[order] = rung.cpu().numpy()
+    np.testing.assert_array_equal(got_rung, rung_ref)
+    dp = got_p - p_ref
+    dp -= np.round(dp)
+    assert np.abs(dp).max() <= 1e-10 * W.x_r
+    assert np.abs(got_q - q_ref).max() <= 1e-10 * np.abs(q_ref).max()

@@ -451,3 +451,24 @@ def test_rung_leapfrog_synchronised_every_step_is_unmerged_kdk():
         q = oracle.kick(q, a, [dt / 2])
     np.testing.assert_array_equal(p1, x)
     np.testing.assert_array_equal(q1, q)
+
+
+def test_rung_leapfrog_with_long_range_is_kdk_of_the_total_force():
+    """One rung, synchronised every step, with the mesh force: kick (dt/2) with the
+    short- and then the long-range force, drift (dt), kick (dt/2) likewise."""
+    from oracle import pm
+    pos = _mixed_positions(1500, seed=9)
+    dt, eta, n_phi = 0.02, 0.025, 32
+    p1, q1, _, _, _ = oracle.rung_leapfrog(pos, np.zeros_like(pos), XS, XR, GM, "bspline", EPS, dt, eta,
+                                           n_rung=1, n_steps=2, period=1, n_phi=n_phi)
+    x = pos.copy()
+    q = np.zeros_like(pos)
+    for step in range(2):
+        for half in range(2):
+            if half == 1:
+                x = oracle.drift(x, q, dt)
+            a, _ = oracle.sr_accel(x, XS, XR, GM, "bspline", EPS)
+            q = oracle.kick(q, a, [dt / 2])
+            q = oracle.kick(q, pm.lr_accel(x, n_phi, XS, GM), [dt / 2])
+    np.testing.assert_array_equal(p1, x)
+    np.testing.assert_array_equal(q1, q)
