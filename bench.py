@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 18, help="receivers in the CPU-oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1 << 14, help="receivers per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["forces32", "forces64", "vjp32", "sort"], default=None,
+    ap.add_argument("--only", choices=["forces32", "forces64", "vjp32", "sort", "pm32"], default=None,
                     help="profiling mode: run just one kernel family (no contract line)")
     return ap.parse_args()
 
@@ -499,6 +499,17 @@ def run_only(args):
     acc64 = torch.zeros((3, w.n), dtype=torch.float64, device=dev)
     abar = torch.randn((3, w.n), dtype=torch.float32, device=dev)
     times = []
+    if args.only == "pm32":
+        from paper_2112_01508_gb300 import LongRange
+        with LongRange.from_workload(w, precision=32, device=dev) as lr:
+            for k in range(args.warmup + args.steps):
+                lr.accel(pos, acc32)
+                st = lr.stats()
+                if k >= args.warmup:
+                    times.append(st.total_ms)
+        print(json.dumps({"only": args.only, "workload": w.name, "mesh_ms": times, "n_phi": w.n_phi}))
+        sr.close()
+        return
     for k in range(args.warmup + args.steps):
         if args.only == "forces32":
             sr.forces(pos, 32, acc32)
