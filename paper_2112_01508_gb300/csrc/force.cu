@@ -32,6 +32,8 @@
 #include <mutex>
 #include <vector>
 
+#include <type_traits>
+
 #include "ctx.cuh"
 #include "erfcx_fit.h"
 #include "pair_math.cuh"
@@ -611,7 +613,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
         const unsigned dpk = dn;
         vn = (b + kWarp < total) ? locate(b + kWarp, jn, dn) : false;
         if (vn) rn = a.rel4[jn];
-        bool keep = false;
+        bool keep = false, near = false;
         Vec3<float> pj = {0.f, 0.f, 0.f};
         if (have) {
           int dx, dy, dz;
@@ -622,7 +624,11 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
           const float tx = fmaxf(fmaxf(F.lo.x - pj.x, pj.x - F.hi.x), 0.f);
           const float ty = fmaxf(fmaxf(F.lo.y - pj.y, pj.y - F.hi.y), 0.f);
           const float tz = fmaxf(fmaxf(F.lo.z - pj.z, pj.z - F.hi.z), 0.f);
-          keep = fmaf(tx, tx, fmaf(ty, ty, tz * tz)) < a.f.margin2_f;
+          const float gap2 = fmaf(tx, tx, fmaf(ty, ty, tz * tz));
+          keep = gap2 < a.f.margin2_f;
+          // can this supplier come closer than r_sw to some receiver?  (the box gap
+          // is a lower bound of every receiver distance)
+          near = keep && gap2 < a.f.rsw2_f;
         }
         const unsigned m = __ballot_sync(full, keep);
         const int nsurv = __popc(m);
@@ -641,6 +647,10 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
         }
         __syncwarp();
         const int npairs = (nsurv + 1) >> 1;
+        // Batches with no supplier within r_sw of the receivers' box run a loop
+        // without the softened-branch test (a vote and a branch per step).
+        auto run_pairs = [&](auto check_soft) {
+          constexpr bool kCheckSoft = decltype(check_soft)::value;
         for (int p = 0; p < npairs; ++p) {
           const float4 s = S.sxy[p];
           const float2 z = S.sz[p];
@@ -665,13 +675,15 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
             } else {
               f2 B = bracket_main_f32x2<SOFT>(r2, a.f);
               upk(B, b0, b1);
-              const bool rare0 = u0 && (q0 < a.f.rsw2_f), rare1 = u1 && (q1 < a.f.rsw2_f);
-              if (__any_sync(full, rare0 || rare1)) {
-                float Ds;
-                const float s0 = bracket_soft_f32<SOFT, false>(q0, a.f, a.sc, Ds);
-                const float s1 = bracket_soft_f32<SOFT, false>(q1, a.f, a.sc, Ds);
-                if (rare0) b0 = s0;
-                if (rare1) b1 = s1;
+              if (kCheckSoft) {
+                const bool rare0 = u0 && (q0 < a.f.rsw2_f), rare1 = u1 && (q1 < a.f.rsw2_f);
+                if (__any_sync(full, rare0 || rare1)) {
+                  float Ds;
+                  const float s0 = bracket_soft_f32<SOFT, false>(q0, a.f, a.sc, Ds);
+                  const float s1 = bracket_soft_f32<SOFT, false>(q1, a.f, a.sc, Ds);
+                  if (rare0) b0 = s0;
+                  if (rare1) b1 = s1;
+                }
               }
             }
             const f2 B = pk(u0 ? b0 : 0.0f, u1 ? b1 : 0.0f);
@@ -680,6 +692,9 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
             az = fma2(B, dz, az);
           }
         }
+        };
+        if (TABLE || __any_sync(full, near)) run_pairs(std::true_type{});
+        else run_pairs(std::false_type{});
         __syncwarp();
       }
     });
