@@ -383,7 +383,8 @@ __device__ __forceinline__ void enumerate_suppliers(const TraversalArgs& a, cons
 // bounding box.
 template <class Real, bool VJP>
 __device__ __forceinline__ bool load_supplier(const TraversalArgs& a, const WarpList& L, int nlist, int f,
-                                              const ChunkFrame<Real>& F, Vec3<Real>& pj, Vec3<Real>& aj) {
+                                              const ChunkFrame<Real>& F, Vec3<Real>& pj, Vec3<Real>& aj,
+                                              Real* gap2_out = nullptr) {
   int lo_e = 0, hi_e = nlist - 1;  // last entry with pre <= f
   while (lo_e < hi_e) {
     int mid = (lo_e + hi_e + 1) >> 1;
@@ -416,7 +417,9 @@ __device__ __forceinline__ bool load_supplier(const TraversalArgs& a, const Warp
   Real tx = fmax(fmax(F.lo.x - pj.x, pj.x - F.hi.x), Real(0));
   Real ty = fmax(fmax(F.lo.y - pj.y, pj.y - F.hi.y), Real(0));
   Real tz = fmax(fmax(F.lo.z - pj.z, pj.z - F.hi.z), Real(0));
-  return (tx * tx + ty * ty + tz * tz) < Real(a.f.margin2_f);
+  const Real gap2 = tx * tx + ty * ty + tz * tz;
+  if (gap2_out) *gap2_out = gap2;
+  return gap2 < Real(a.f.margin2_f);
 }
 
 // Generic path (FP64 forward, and the adjoint in both precisions): every
@@ -755,8 +758,12 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_vjp_packed(Trav
       for (int b = 0; b < total; b += kWarp) {
         const int f = b + lane;
         Vec3<float> pj = {0.f, 0.f, 0.f}, aj = {0.f, 0.f, 0.f};
-        bool keep = false;
-        if (f < total) keep = load_supplier<float, true>(a, S.L, nlist, f, F, pj, aj);
+        bool keep = false, near = false;
+        if (f < total) {
+          float gap2;
+          keep = load_supplier<float, true>(a, S.L, nlist, f, F, pj, aj, &gap2);
+          near = keep && gap2 < a.f.rsw2_f;  // may come within r_sw of a receiver (or coincide)
+        }
         const unsigned m = __ballot_sync(full, keep);
         const int nsurv = __popc(m);
         if (keep) {
@@ -780,6 +787,10 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_vjp_packed(Trav
         }
         __syncwarp();
         const int npairs = (nsurv + 1) >> 1;
+        // as in the forward kernel: batches with no supplier within r_sw of the
+        // receivers' box skip the softened-branch test
+        auto run_pairs = [&](auto check_soft) {
+          constexpr bool kCheckSoft = decltype(check_soft)::value;
         for (int p = 0; p < npairs; ++p) {
           const float4 s = S.sxy[p];
           const float2 z = S.sz[p];
@@ -804,13 +815,15 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_vjp_packed(Trav
             float b0, b1, d0, d1;
             upk(B, b0, b1);
             upk(D, d0, d1);
-            const bool rare0 = h0 && (q0 < a.f.rsw2_f), rare1 = h1 && (q1 < a.f.rsw2_f);
-            if (__any_sync(full, rare0 || rare1)) {
-              float Ds0, Ds1;
-              const float s0 = bracket_soft_f32<SOFT, true>(q0, a.f, a.sc, Ds0);
-              const float s1 = bracket_soft_f32<SOFT, true>(q1, a.f, a.sc, Ds1);
-              if (rare0) { b0 = s0; d0 = Ds0; }
-              if (rare1) { b1 = s1; d1 = Ds1; }
+            if (kCheckSoft) {
+              const bool rare0 = h0 && (q0 < a.f.rsw2_f), rare1 = h1 && (q1 < a.f.rsw2_f);
+              if (__any_sync(full, rare0 || rare1)) {
+                float Ds0, Ds1;
+                const float s0 = bracket_soft_f32<SOFT, true>(q0, a.f, a.sc, Ds0);
+                const float s1 = bracket_soft_f32<SOFT, true>(q1, a.f, a.sc, Ds1);
+                if (rare0) { b0 = s0; d0 = Ds0; }
+                if (rare1) { b1 = s1; d1 = Ds1; }
+              }
             }
             B = pk(h0 ? b0 : 0.0f, h1 ? b1 : 0.0f);
             D = pk(h0 ? d0 : 0.0f, h1 ? d1 : 0.0f);
@@ -821,6 +834,9 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_vjp_packed(Trav
             gz = fma2(B, vz2, fma2(cc, dz, gz));
           }
         }
+        };
+        if (__any_sync(full, near)) run_pairs(std::true_type{});
+        else run_pairs(std::false_type{});
         __syncwarp();
       }
     });
