@@ -506,7 +506,8 @@ def run_only(args):
                 lr.accel(pos, acc32)
                 st = lr.stats()
                 if k >= args.warmup:
-                    times.append(st.total_ms)
+                    times.append({"total": st.total_ms, "assign": st.assign_ms, "fft": st.fft_ms,
+                                  "green": st.kernel_ms, "ifft": st.ifft_ms, "interp": st.interp_ms})
         print(json.dumps({"only": args.only, "workload": w.name, "mesh_ms": times, "n_phi": w.n_phi}))
         sr.close()
         return
