@@ -73,6 +73,8 @@ def assign(pos, n_phi: int, p_i: int = 2, box: float = 1.0):
         for b in range(6):
             for c in range(6):
                 wt = w[0, :, a] * w[1, :, b] * w[2, :, c]
+                if not wt.any():
+                    continue  # outside W_p's support for every particle
                 np.add.at(rho, (cells[0, :, a], cells[1, :, b], cells[2, :, c]), wt)
     return rho
 
@@ -85,7 +87,10 @@ def interpolate(grid, pos, p_i: int = 2, box: float = 1.0):
     for a in range(6):
         for b in range(6):
             for c in range(6):
-                out += w[0, :, a] * w[1, :, b] * w[2, :, c] * grid[cells[0, :, a], cells[1, :, b], cells[2, :, c]]
+                wt = w[0, :, a] * w[1, :, b] * w[2, :, c]
+                if not wt.any():
+                    continue
+                out += wt * grid[cells[0, :, a], cells[1, :, b], cells[2, :, c]]
     return out
 
 

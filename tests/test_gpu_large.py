@@ -27,6 +27,34 @@ def test_n2m_full_parity():
     assert abs(r32["pairs"] - pairs) <= 1e-6 * pairs
 
 
+def test_n2m_mesh_parity():
+    """The long-range mesh force of the benchmark set (128^3 particles, 256^3 mesh, CIC,
+    D_4) against the PM oracle: full density and potential, accelerations compared on
+    a seeded sample of 2^16 particles."""
+    import torch
+
+    from oracle import pm as opm
+    from paper_2112_01508_gb300 import LongRange
+
+    w = synth.workload("n2m")
+    pos = synth.workload_positions(w)
+    idx = np.sort(np.random.default_rng(3).choice(w.n, 1 << 16, replace=False))
+    phi = opm.potential_mesh(opm.assign(pos, w.n_phi, 2), w.x_s, 2)
+    ref = np.empty((3, len(idx)))
+    for d in range(3):
+        ref[d] = opm.interpolate(opm.difference(phi, 4, d), pos[:, idx], 2)
+    ref *= 4 * np.pi * w.G_m * w.n_phi ** 4
+    p = torch.from_numpy(pos).cuda()
+    for prec, tol in ((64, 1e-12), (32, 1e-5)):
+        with LongRange.from_workload(w, precision=prec) as lr:
+            a = lr.accel(p)
+            lr.sync()
+            got = a.double().cpu().numpy()[:, idx]
+        err = rel_rms(got, ref)
+        print(f"n2m mesh fp{prec}: rel RMS {err:.3e} over {len(idx)} particles")
+        assert err <= tol
+
+
 def test_n134m_sampled_with_rungs():
     """512^3: rungs from the FP64 fake kick (bit-exact vs the oracle's rule on the
     same accelerations), then the FP32 and FP64 forces of the active rungs on
