@@ -442,9 +442,15 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, secs, cp, nrecv, cores = cpu_oracle_rate(w, pos_np, args.cpu_sample)
+        import oracle
+        oracle.set_num_threads(1)
+        rate1, secs1, cp1, nrecv1, _ = cpu_oracle_rate(w, pos_np, max(args.cpu_sample // 16, 1))
+        oracle.set_num_threads(cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{nrecv} seeded receivers of the {w.n}-particle set (all suppliers), {cp} pairs, "
-                         f"{secs:.1f} s wall"}
+                         f"{secs:.1f} s wall",
+               "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                               "sample": f"{nrecv1} seeded receivers, {cp1} pairs, {secs1:.1f} s"}}
 
     sr.close()
     if rank == 0:

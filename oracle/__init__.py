@@ -77,6 +77,8 @@ def _load():
             lib.oracle_rung_kick.restype = i64
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = i
+            lib.oracle_set_num_threads.argtypes = [i]
+            lib.oracle_set_num_threads.restype = None
             _lib = lib
     return _lib
 
@@ -96,6 +98,11 @@ def _soft(s):
 
 def num_threads() -> int:
     return _load().oracle_num_threads()
+
+
+def set_num_threads(k: int) -> None:
+    """Threads used by the oracle's parallel loops from now on."""
+    _load().oracle_set_num_threads(int(k))
 
 
 def bracket(r, x_s, softening="bspline", eps=0.0):

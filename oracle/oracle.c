@@ -552,3 +552,12 @@ int oracle_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the following parallel loops (timing of the single-threaded oracle). */
+void oracle_set_num_threads(int k) {
+#ifdef _OPENMP
+  if (k > 0) omp_set_num_threads(k);
+#else
+  (void)k;
+#endif
+}
