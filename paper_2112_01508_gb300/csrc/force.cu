@@ -547,6 +547,16 @@ __global__ void __launch_bounds__(kForceThreads) k_traverse(TraversalArgs a) {
 
 constexpr int kPThreads = 128;
 constexpr int kPWarps = kPThreads / kWarp;
+constexpr float kR2Floor = 1e-24f;    // added to r^2 in the packed forward kernel
+constexpr float kR2Self = 1e-23f;     // r^2 below this: a zero displacement
+constexpr float kCutScale = 0x1p64f;  // cutoff mask: sat((x_r^2 - r^2) 2^64)
+
+// saturate(a * b + c) in one FP32 instruction
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+  float d;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
 
 struct PackedSmem {
   WarpList L;
@@ -574,6 +584,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
   PackedSmem& S = smem[threadIdx.x >> 5];
   const int n_chunks = *a.n_chunks;
   const float xr2 = a.f.xr2_f;
+  const float xr2s = xr2 * kCutScale;
   unsigned long long pair_total = 0;
   for (;;) {
     const int c = next_chunk(a, lane);
@@ -582,7 +593,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
     load_chunk<float>(a, a.chunks[c], lane, F);
     const f2 px = pk(F.pi.x, F.pi.x), py = pk(F.pi.y, F.pi.y), pz = pk(F.pi.z, F.pi.z);
     f2 ax = pk(0.f, 0.f), ay = pk(0.f, 0.f), az = pk(0.f, 0.f);
-    int hits = 0;
+    f2 hitsf = pk(0.f, 0.f);  // interacting pairs of this lane (exact integers in FP32)
     enumerate_suppliers<float>(a, F, S.L, lane, [&](int nlist, int total) {
       float* sxy = (float*)S.sxy;
       float* sz = (float*)S.sz;
@@ -642,11 +653,11 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
           sxy[4 * p + 2 + h] = -pj.y;
           sz[2 * p + h] = -pj.z;
         }
-        if (lane == 0 && (nsurv & 1)) {  // pad the last pair far from every receiver
+        if (lane == 0 && (nsurv & 1)) {  // pad the last pair far from every receiver (finite B there)
           const int p = nsurv >> 1;
-          sxy[4 * p + 1] = 1e30f;
-          sxy[4 * p + 3] = 1e30f;
-          sz[2 * p + 1] = 1e30f;
+          sxy[4 * p + 1] = 1e10f;
+          sxy[4 * p + 3] = 1e10f;
+          sz[2 * p + 1] = 1e10f;
         }
         __syncwarp();
         const int npairs = (nsurv + 1) >> 1;
@@ -660,36 +671,41 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
           const f2 dx = add2(px, pk(s.x, s.y));
           const f2 dy = add2(py, pk(s.z, s.w));
           const f2 dz = add2(pz, pk(z.x, z.y));
-          const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+          // r^2 + 1e-24: a zero displacement (the receiver itself, coincident
+          // particles) gets a large but finite B and contributes B * 0 = 0; the
+          // offset is far below one ulp of the r^2 near the cutoff, and below the
+          // square of the smallest non-zero displacement of subtile-relative FP32
+          // coordinates, so no cutoff decision changes
+          const f2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, pk(kR2Floor, kR2Floor))));
           float q0, q1;
           upk(r2, q0, q1);
           const bool h0 = q0 < xr2, h1 = q1 < xr2;
           if (__any_sync(full, h0 || h1)) {
-            hits += (int)h0 + (int)h1;
-            // r^2 = 0 (the receiver itself, coincident particles) contributes nothing;
-            // lanes that do not use a half drop its (possibly non-finite) value below
-            const bool u0 = h0 && q0 > 0.0f, u1 = h1 && q1 > 0.0f;
-            float b0, b1;
+            // cutoff mask in the FP32 pipe: 1 iff r^2 < x_r^2 (exact: the scale is a power of two)
+            const f2 c = pk(fma_sat(q0, -kCutScale, xr2s), fma_sat(q1, -kCutScale, xr2s));
+            hitsf = add2(hitsf, c);
+            f2 B;
             if (TABLE) {  // nearest-grid-point lookup in r^2 (softening included)
               const int i0 = min((int)(fminf(q0, a.f.xr2_f) * a.table_scale), a.n_table - 1);
               const int i1 = min((int)(fminf(q1, a.f.xr2_f) * a.table_scale), a.n_table - 1);
-              b0 = tab[max(i0, 0)];
-              b1 = tab[max(i1, 0)];
+              B = pk(tab[max(i0, 0)], tab[max(i1, 0)]);
             } else {
-              f2 B = bracket_main_f32x2<SOFT>(r2, a.f);
-              upk(B, b0, b1);
+              B = bracket_main_f32x2<SOFT>(r2, a.f);
               if (kCheckSoft) {
-                const bool rare0 = u0 && (q0 < a.f.rsw2_f), rare1 = u1 && (q1 < a.f.rsw2_f);
+                const bool rare0 = h0 && (q0 < a.f.rsw2_f) && (q0 > kR2Self);
+                const bool rare1 = h1 && (q1 < a.f.rsw2_f) && (q1 > kR2Self);
                 if (__any_sync(full, rare0 || rare1)) {
-                  float Ds;
+                  float b0, b1, Ds;
+                  upk(B, b0, b1);
                   const float s0 = bracket_soft_f32<SOFT, false>(q0, a.f, a.sc, Ds);
                   const float s1 = bracket_soft_f32<SOFT, false>(q1, a.f, a.sc, Ds);
                   if (rare0) b0 = s0;
                   if (rare1) b1 = s1;
+                  B = pk(b0, b1);
                 }
               }
             }
-            const f2 B = pk(u0 ? b0 : 0.0f, u1 ? b1 : 0.0f);
+            B = mul2(B, c);
             ax = fma2(B, dx, ax);
             ay = fma2(B, dy, ay);
             az = fma2(B, dz, az);
@@ -710,7 +726,8 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
     upk(az, l, h);
     acc.z = l + h;
     store_result<float>(a, F, acc);
-    hits = F.valid ? hits - 1 : 0;  // the receiver met itself once (r = 0)
+    upk(hitsf, l, h);
+    const int hits = F.valid ? (int)(l + h) - 1 : 0;  // the receiver met itself once (r = 0)
     pair_total += (unsigned long long)__reduce_add_sync(full, (unsigned)hits);
   }
   if (lane == 0 && pair_total) atomicAdd(a.pairs, pair_total);
