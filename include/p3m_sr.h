@@ -178,10 +178,11 @@ p3m_status p3m_sr_build_pairs(p3m_sr_ctx* ctx, const int8_t* rung, int rung_min)
 /*
  * Short-range accelerations (Section 2.1.3, short-range half of Eq.
  * p3m_gravity) on the receivers of the last p3m_sr_build_pairs.
- *   pos        3 x n float64 SoA, device, in the sorted order and unchanged
- *              since the last p3m_sr_sort (the sort already wrote the FP32
- *              subtile-relative records of that array; a different array is
- *              re-read here).
+ *   pos        3 x n float64 SoA, device, in the sorted order, unchanged
+ *              since the last p3m_sr_sort or moved only by p3m_sr_drift (the
+ *              sort wrote the FP32 subtile-relative records of that array;
+ *              after a drift, or for a different array, they are rebuilt
+ *              here).
  *   precision  32: FP32 arithmetic and accumulation, displacements taken
  *              relative to subtile origins (positions read once in FP64);
  *              acc_out is 3 x n float.  64: FP64 throughout, acc_out 3 x n
@@ -262,7 +263,14 @@ p3m_status p3m_sr_rung_kick(p3m_sr_ctx* ctx, void* mom, int mom_precision, const
  * Drift (Section 2.2.2, operator D with a = 1):
  *   x_i <- x_i + q_i * factor, then wrapped into [0, L): x <- x - L floor(x / L).
  *   pos  3 x n float64 device;  mom  3 x n device, mom_precision 32 or 64.
- * Drifting changes subtile membership: sort again before the next forces call.
+ * Drifting the array of the last p3m_sr_sort keeps that sort usable, as the
+ * paper's periodic (not per-step) memory reordering does (Section 2.1.3,
+ * "Other optimisations"): the drift records a bound on its largest
+ * displacement, and build_pairs / forces / vjp widen the subtile reach by the
+ * sum of the bounds since the sort (more candidates, same pairs).  After 64
+ * such drifts the sort is dropped (P3M_ERR_STATE until the next p3m_sr_sort);
+ * a total drift with x_r + 2 drift >= L/2 latches P3M_ERR_STATE in the next
+ * traversal.  Drifting any other array does not touch the sort.
  */
 p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom, int mom_precision,
                         double factor);

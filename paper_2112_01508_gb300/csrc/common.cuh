@@ -10,6 +10,7 @@
 namespace p3m {
 
 constexpr int kWarp = 32;
+constexpr int kMaxDrifts = 64;  // drifts of the sorted positions allowed between two sorts
 constexpr int kChunk = 32;  // receivers per chunk (one warp lane each)
 
 // Device-side error bits, latched in a device word by the kernels.
@@ -17,6 +18,7 @@ enum : int {
   kErrPosition = 1,      // non-finite or out-of-box position at binning
   kErrNonfiniteAcc = 2,  // non-finite acceleration at rung assignment
   kErrRungState = 4,     // rung outside [0, n_rung) or kick state outside {0, 1, 2} at a rung kick
+  kErrDrift = 8,         // positions drifted so far since the sort that the traversal cannot cover them
 };
 
 // Tile/subtile geometry of the periodic box (Section 2.1.3).

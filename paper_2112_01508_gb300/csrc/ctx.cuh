@@ -64,6 +64,9 @@ struct p3m_sr_ctx {
   // ---- state ----
   bool sorted = false;
   const double* sorted_pos = nullptr;  // array sorted by the last p3m_sr_sort (rel4 matches it)
+  float* drift_slots = nullptr;        // kMaxDrifts: largest displacement of each drift since the sort
+  int n_drift = 0;                     // drifts applied to sorted_pos since the sort
+  bool rel4_stale = false;             // sorted_pos moved after rel4 was written
   bool pairs_built = false;
   bool all_chunks_built = false;
   bool all_active = true;

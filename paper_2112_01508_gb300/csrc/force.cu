@@ -61,10 +61,16 @@ __global__ void k_rel4(const double* __restrict__ pos, const int* __restrict__ c
   int id = cell[i];
   int gx, gy, gz;
   decode_subtile(g, id, gx, gy, gz);
-  float rx = (float)__fma_rn(-(double)gx, g.side64[0], pos[i]);
-  float ry = (float)__fma_rn(-(double)gy, g.side64[1], pos[n + i]);
-  float rz = (float)__fma_rn(-(double)gz, g.side64[2], pos[2 * n + i]);
-  rel4[i] = make_float4(rx, ry, rz, __int_as_float(id));
+  // relative to the origin of the subtile of the last sort; a particle that
+  // drifted across the periodic boundary since then takes its nearest image
+  double r[3] = {__fma_rn(-(double)gx, g.side64[0], pos[i]), __fma_rn(-(double)gy, g.side64[1], pos[n + i]),
+                 __fma_rn(-(double)gz, g.side64[2], pos[2 * n + i])};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (r[d] > 0.5 * g.box) r[d] -= g.box;
+    else if (r[d] < -0.5 * g.box) r[d] += g.box;
+  }
+  rel4[i] = make_float4((float)r[0], (float)r[1], (float)r[2], __int_as_float(id));
 }
 
 __global__ void k_active_flags(const int8_t* __restrict__ rung, int64_t n, int rung_min, int8_t* __restrict__ flag,
@@ -180,6 +186,9 @@ struct TraversalArgs {
   const int* offsets;         // S + 1 subtile offsets
   const int* cell;            // sorted subtile ids
   const Chunk* chunks;
+  const float* drift_slots;   // displacement bounds of the drifts since the sort (device)
+  int n_drift;                // how many of them
+  int* err;                   // device error bits (kErrDrift), or nullptr
   const int* n_chunks;        // device count
   int* counter;               // dynamic chunk counter (zeroed before launch)
   const int* active_idx;      // receiver list (nullptr: chunk ranges are particle indices)
@@ -239,6 +248,44 @@ struct WarpList {
   unsigned delta[kListCap];
 };
 
+// Reach of the traversal.  Right after a sort: the block R of subtiles around the
+// receivers' subtiles and the pruning bound x_r on the gap between a candidate
+// subtile box and the receivers' box.  After drifts of total length delta since
+// the sort, a particle may lie up to delta outside the subtile it was sorted into:
+// the gap bound grows to x_r + delta and the block to x_r + 2 delta (receivers and
+// suppliers both moved).
+struct Reach {
+  int R[3];
+  float sub2;     // squared gap bound, FP32 path
+  double sub2_d;  // FP64 path
+};
+
+__device__ __forceinline__ Reach make_reach(const TraversalArgs& a) {
+  Reach r;
+  float delta = 0.0f;
+  for (int k = 0; k < a.n_drift; ++k) delta += a.drift_slots[k];
+  if (!(delta > 0.0f)) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) r.R[d] = a.g.R[d];
+    r.sub2 = a.f.margin2_f;
+    r.sub2_d = (double)a.f.margin2_f;
+    return r;
+  }
+  const double dl = (double)delta * (1.0 + 1e-5);  // the float sum may round down
+  const double reach = sqrt((double)a.f.margin2_f) + dl;
+  if (!(reach + dl < 0.5 * a.g.box)) {
+    if ((threadIdx.x & 31) == 0 && a.err) atomicOr(a.err, kErrDrift);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double rr = fmin(reach + dl, 0.5 * a.g.box);
+    r.R[d] = (int)ceil(rr / a.g.side64[d] * (1.0 + 1e-12));
+  }
+  r.sub2_d = reach * reach;
+  r.sub2 = (float)(r.sub2_d * (1.0 + 1e-6));
+  return r;
+}
+
 // The receivers of one chunk in its frame: positions, bounding box, subtile block.
 template <class Real>
 struct ChunkFrame {
@@ -252,7 +299,8 @@ struct ChunkFrame {
 };
 
 template <class Real>
-__device__ __forceinline__ void load_chunk(const TraversalArgs& a, const Chunk& ch, int lane, ChunkFrame<Real>& F) {
+__device__ __forceinline__ void load_chunk(const TraversalArgs& a, const Reach& rc, const Chunk& ch, int lane,
+                                           ChunkFrame<Real>& F) {
   const unsigned full = 0xffffffffu;
   const Geometry& g = a.g;
   F.valid = lane < ch.count;
@@ -281,6 +329,11 @@ __device__ __forceinline__ void load_chunk(const TraversalArgs& a, const Chunk& 
     F.pi.x = F.valid ? a.pos[F.pidx] : 0.0;
     F.pi.y = F.valid ? a.pos[a.n + F.pidx] : 0.0;
     F.pi.z = F.valid ? a.pos[2 * a.n + F.pidx] : 0.0;
+    if (a.n_drift > 0 && F.valid) {  // drifted since the sort: the image nearest its sorted subtile
+      F.pi.x += g.box * rint(((gi[0] + 0.5) * g.side64[0] - F.pi.x) / g.box);
+      F.pi.y += g.box * rint(((gi[1] + 0.5) * g.side64[1] - F.pi.y) / g.box);
+      F.pi.z += g.box * rint(((gi[2] + 0.5) * g.side64[2] - F.pi.z) / g.box);
+    }
   }
   const Real big = Real(1e30);
   F.lo.x = warp_min(F.valid ? F.pi.x : big);
@@ -292,8 +345,8 @@ __device__ __forceinline__ void load_chunk(const TraversalArgs& a, const Chunk& 
   if (!F.valid) { F.pi.x = big; F.pi.y = big; F.pi.z = big; }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    F.elo[d] = __reduce_min_sync(full, F.valid ? e[d] : 1 << 20) - g.R[d];
-    int ehi = __reduce_max_sync(full, F.valid ? e[d] : -(1 << 20)) + g.R[d];
+    F.elo[d] = __reduce_min_sync(full, F.valid ? e[d] : 1 << 20) - rc.R[d];
+    int ehi = __reduce_max_sync(full, F.valid ? e[d] : -(1 << 20)) + rc.R[d];
     F.ext[d] = ehi - F.elo[d] + 1;
     if constexpr (sizeof(Real) == 4) F.org[d] = 0.0f;
     else F.org[d] = (double)F.g0[d] * g.side64[d];
@@ -305,8 +358,8 @@ __device__ __forceinline__ void load_chunk(const TraversalArgs& a, const Chunk& 
 // receivers' bounding box is below x_r and that hold particles, and append their
 // particle ranges to the warp's list; `proc(nlist, total)` consumes a full list.
 template <class Real, class Proc>
-__device__ __forceinline__ void enumerate_suppliers(const TraversalArgs& a, const ChunkFrame<Real>& F, WarpList& L,
-                                                    int lane, Proc&& proc) {
+__device__ __forceinline__ void enumerate_suppliers(const TraversalArgs& a, const Reach& rc, const ChunkFrame<Real>& F,
+                                                    WarpList& L, int lane, Proc&& proc) {
   const unsigned full = 0xffffffffu;
   const Geometry& g = a.g;
   const int ncand = F.ext[0] * F.ext[1] * F.ext[2];
@@ -334,7 +387,9 @@ __device__ __forceinline__ void enumerate_suppliers(const TraversalArgs& a, cons
         Real gp = fmax(fmax(blo[d] - jhi, jlo - bhi[d]), Real(0));
         gap2 += gp * gp;
       }
-      if (gap2 < Real(a.f.margin2_f)) {
+      Real sub2;
+      if constexpr (sizeof(Real) == 4) sub2 = rc.sub2; else sub2 = rc.sub2_d;
+      if (gap2 < sub2) {
         int gx = F.g0[0] + dx, gy = F.g0[1] + dy, gz = F.g0[2] + dz;
         gx += gx < 0 ? g.M[0] : (gx >= g.M[0] ? -g.M[0] : 0);
         gy += gy < 0 ? g.M[1] : (gy >= g.M[1] ? -g.M[1] : 0);
@@ -410,6 +465,11 @@ __device__ __forceinline__ bool load_supplier(const TraversalArgs& a, const Warp
     pj.x = a.pos[j] + sx;
     pj.y = a.pos[a.n + j] + sy;
     pj.z = a.pos[2 * a.n + j] + sz;
+    if (a.n_drift > 0) {  // drifted since the sort: the image nearest the candidate subtile
+      pj.x += a.g.box * rint(((gx + 0.5) * a.g.side64[0] - pj.x) / a.g.box);
+      pj.y += a.g.box * rint(((gy + 0.5) * a.g.side64[1] - pj.y) / a.g.box);
+      pj.z += a.g.box * rint(((gz + 0.5) * a.g.side64[2] - pj.z) / a.g.box);
+    }
     if (VJP) {
       aj.x = a.abar_d[j]; aj.y = a.abar_d[a.n + j]; aj.z = a.abar_d[2 * a.n + j];
     }
@@ -510,12 +570,13 @@ __global__ void __launch_bounds__(kForceThreads) k_traverse(TraversalArgs a) {
   const int lane = threadIdx.x & 31;
   WarpList& L = lists[threadIdx.x >> 5];
   const int n_chunks = *a.n_chunks;
+  const Reach rc = make_reach(a);
   unsigned long long pair_total = 0;
   for (;;) {
     const int c = next_chunk(a, lane);
     if (c >= n_chunks) break;
     ChunkFrame<Real> F;
-    load_chunk<Real>(a, a.chunks[c], lane, F);
+    load_chunk<Real>(a, rc, a.chunks[c], lane, F);
     Vec3<Real> abar_i = {Real(0), Real(0), Real(0)};
     if (VJP && F.valid) {
       if constexpr (sizeof(Real) == 4) {
@@ -527,7 +588,7 @@ __global__ void __launch_bounds__(kForceThreads) k_traverse(TraversalArgs a) {
     }
     Vec3<Real> acc = {Real(0), Real(0), Real(0)};
     int hits = 0;
-    enumerate_suppliers<Real>(a, F, L, lane, [&](int nlist, int total) {
+    enumerate_suppliers<Real>(a, rc, F, L, lane, [&](int nlist, int total) {
       process_list<Real, VJP, SOFT>(a, L, nlist, total, lane, F, abar_i, acc, hits);
     });
     store_result<Real>(a, F, acc);
@@ -583,6 +644,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
   const int lane = threadIdx.x & 31;
   PackedSmem& S = smem[threadIdx.x >> 5];
   const int n_chunks = *a.n_chunks;
+  const Reach rc = make_reach(a);
   const float xr2 = a.f.xr2_f;
   const float xr2s = xr2 * kCutScale;
   unsigned long long pair_total = 0;
@@ -590,11 +652,11 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
     const int c = next_chunk(a, lane);
     if (c >= n_chunks) break;
     ChunkFrame<float> F;
-    load_chunk<float>(a, a.chunks[c], lane, F);
+    load_chunk<float>(a, rc, a.chunks[c], lane, F);
     const f2 px = pk(F.pi.x, F.pi.x), py = pk(F.pi.y, F.pi.y), pz = pk(F.pi.z, F.pi.z);
     f2 ax = pk(0.f, 0.f), ay = pk(0.f, 0.f), az = pk(0.f, 0.f);
     f2 hitsf = pk(0.f, 0.f);  // interacting pairs of this lane (exact integers in FP32)
-    enumerate_suppliers<float>(a, F, S.L, lane, [&](int nlist, int total) {
+    enumerate_suppliers<float>(a, rc, F, S.L, lane, [&](int nlist, int total) {
       float* sxy = (float*)S.sxy;
       float* sz = (float*)S.sz;
       const WarpList& L = S.L;
@@ -754,20 +816,21 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_vjp_packed(Trav
   const int lane = threadIdx.x & 31;
   PackedVjpSmem& S = smem[threadIdx.x >> 5];
   const int n_chunks = *a.n_chunks;
+  const Reach rc = make_reach(a);
   const float xr2 = a.f.xr2_f;
   unsigned long long pair_total = 0;
   for (;;) {
     const int c = next_chunk(a, lane);
     if (c >= n_chunks) break;
     ChunkFrame<float> F;
-    load_chunk<float>(a, a.chunks[c], lane, F);
+    load_chunk<float>(a, rc, a.chunks[c], lane, F);
     const f2 px = pk(F.pi.x, F.pi.x), py = pk(F.pi.y, F.pi.y), pz = pk(F.pi.z, F.pi.z);
     float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
     if (F.valid) ab = a.abar4[F.pidx];
     const f2 vix = pk(ab.x, ab.x), viy = pk(ab.y, ab.y), viz = pk(ab.z, ab.z);
     f2 gx = pk(0.f, 0.f), gy = pk(0.f, 0.f), gz = pk(0.f, 0.f);
     int hits = 0;
-    enumerate_suppliers<float>(a, F, S.L, lane, [&](int nlist, int total) {
+    enumerate_suppliers<float>(a, rc, F, S.L, lane, [&](int nlist, int total) {
       float* sxy = (float*)S.sxy;
       float* sz = (float*)S.sz;
       float* vxy = (float*)S.vxy;
@@ -972,14 +1035,18 @@ static TraversalArgs base_args(p3m_sr_ctx* ctx) {
   a.n = ctx->n;
   a.rel4 = ctx->rel4;
   a.pairs = ctx->pair_count;
+  a.drift_slots = ctx->drift_slots;
+  a.n_drift = ctx->n_drift;
+  a.err = ctx->err_dev;
   return a;
 }
 
 static p3m_status prepare_rel4(p3m_sr_ctx* ctx, const double* pos) {
   if (ctx->n == 0) return P3M_OK;
-  if (pos == ctx->sorted_pos) return P3M_OK;  // written by the sort for these positions
+  if (pos == ctx->sorted_pos && !ctx->rel4_stale) return P3M_OK;  // written by the sort for these positions
   k_rel4<<<blocks_for(ctx->n, 256), 256, 0, ctx->stream>>>(pos, ctx->cell, ctx->n, ctx->geo, ctx->rel4);
   ++ctx->launches;
+  if (pos == ctx->sorted_pos) ctx->rel4_stale = false;
   return cuda_check(ctx, cudaGetLastError(), "rel4 kernel");
 }
 

@@ -26,6 +26,8 @@ static p3m_status status_from_bits(p3m_sr_ctx* ctx, int bits) {
     return fail(ctx, P3M_ERR_NONFINITE, "a position was non-finite or outside [0, L) when binned");
   if (bits & kErrNonfiniteAcc)
     return fail(ctx, P3M_ERR_NONFINITE, "a non-finite acceleration was met by the rung assignment");
+  if (bits & kErrDrift)
+    return fail(ctx, P3M_ERR_STATE, "positions drifted too far since the last sort (x_r + 2 drift >= L/2): sort again");
   if (bits & kErrRungState)
     return fail(ctx, P3M_ERR_STATE, "a rung kick met a rung outside [0, n_rung) or a kick state outside {0, 1, 2}");
   return P3M_OK;
@@ -310,6 +312,7 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
   P3M_ALLOC(ctx->pair_count, 2);
   P3M_ALLOC(ctx->rel4, n);
   P3M_ALLOC(ctx->err_dev, 1);
+  P3M_ALLOC(ctx->drift_slots, kMaxDrifts);
 #undef P3M_ALLOC
   if (cudaMallocHost((void**)&ctx->err_host, sizeof(int)) != cudaSuccess) {
     st = fail(ctx, P3M_ERR_OOM, "cudaMallocHost failed");
@@ -326,6 +329,9 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
       goto fail_alloc;
     }
   if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), ctx->stream), "memset")) != P3M_OK)
+    goto fail_alloc;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->drift_slots, 0, sizeof(float) * kMaxDrifts, ctx->stream),
+                       "memset")) != P3M_OK)
     goto fail_alloc;
   if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dev_small, 0, 16 * sizeof(int), ctx->stream), "memset")) != P3M_OK)
     goto fail_alloc;
@@ -391,7 +397,7 @@ extern "C" void p3m_sr_destroy(p3m_sr_ctx* ctx) {
   void* ptrs[] = {ctx->keys[0], ctx->keys[1], ctx->vals[0], ctx->vals[1], ctx->offsets, ctx->hist,
                   ctx->scan_scratch, ctx->gather_tmp, ctx->active_flag, ctx->act_scan, ctx->active_idx,
                   ctx->tile_chunks, ctx->chunks, ctx->chunks_all, ctx->dev_small, ctx->pair_count,
-                  ctx->rel4, ctx->abar4, ctx->abar_d, ctx->table, ctx->err_dev};
+                  ctx->rel4, ctx->abar4, ctx->abar_d, ctx->table, ctx->err_dev, ctx->drift_slots};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->err_host) cudaFreeHost(ctx->err_host);

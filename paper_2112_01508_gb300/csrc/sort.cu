@@ -280,7 +280,9 @@ extern "C" p3m_status p3m_sr_sort(p3m_sr_ctx* ctx, double* pos, void* const* car
   report_latched(ctx);
   ctx->sorted = true;
   ctx->sorted_pos = pos;  // the FP32 records in ctx->rel4 describe these positions
-  return P3M_OK;
+  ctx->n_drift = 0;       // no displacement since this sort
+  ctx->rel4_stale = false;
+  return cuda_check(ctx, cudaMemsetAsync(ctx->drift_slots, 0, sizeof(float) * kMaxDrifts, s), "memset");
 }
 
 static p3m_status permute_rows(p3m_sr_ctx* ctx, const void* src, void* dst, int elem_bytes, int rows, int to_sorted,

@@ -58,19 +58,33 @@ __global__ void k_kick(M* __restrict__ mom, const A* __restrict__ acc, const int
   }
 }
 
+// disp (optional): receives, by atomic max, an upper bound of the largest
+// displacement |q| |factor| of this drift (non-negative floats order as integers).
 template <class M>
-__global__ void k_drift(double* __restrict__ pos, const M* __restrict__ mom, int64_t n, double factor, double box) {
+__global__ void k_drift(double* __restrict__ pos, const M* __restrict__ mom, int64_t n, double factor, double box,
+                        float* __restrict__ disp) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  float my = 0.0f;
+  if (i < n) {
+    double q2 = 0.0;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    double v = __dadd_rn(pos[d * n + i], __dmul_rn((double)mom[d * n + i], factor));
-    const long long vb = __double_as_longlong(v);
-    if (!(vb >= 0 && vb < __double_as_longlong(box))) {  // v - L floor(v / L); floor is 0 inside the box
-      v = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
-      if (v >= box || v < 0.0) v = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double q = (double)mom[d * n + i];
+      q2 = fma(q, q, q2);
+      double v = __dadd_rn(pos[d * n + i], __dmul_rn(q, factor));
+      const long long vb = __double_as_longlong(v);
+      if (!(vb >= 0 && vb < __double_as_longlong(box))) {  // v - L floor(v / L); floor is 0 inside the box
+        v = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
+        if (v >= box || v < 0.0) v = 0.0;
+      }
+      pos[d * n + i] = v;
     }
-    pos[d * n + i] = v;
+    my = (float)(sqrt(q2) * fabs(factor) * (1.0 + 1e-6));
+    if (!(my < 3.0e38f)) my = 3.0e38f;  // non-finite momenta: the bound saturates
+  }
+  if (disp) {
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(my));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned*)disp, m);
   }
 }
 
@@ -193,16 +207,27 @@ extern "C" p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom
   p3m_status st = poll_latched(ctx);
   if (st != P3M_OK) return st;
   if (ctx->n == 0) return P3M_OK;
+  // Drifting the sorted positions keeps the sort usable: the displacement bound of
+  // each drift is recorded and the pair traversal widens its reach by their sum,
+  // until kMaxDrifts drifts, after which a new sort is required.
+  float* slot = nullptr;
+  if (ctx->sorted && pos == ctx->sorted_pos) {
+    if (ctx->n_drift < kMaxDrifts) {
+      slot = ctx->drift_slots + ctx->n_drift++;
+      ctx->rel4_stale = true;
+    } else {
+      ctx->sorted = false;
+      ctx->pairs_built = false;
+      ctx->sorted_pos = nullptr;
+    }
+  }
   const int t = 256;
   if (mom_precision == 64)
     { k_drift<double><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>(pos, (const double*)mom, ctx->n, factor,
-                                                                  ctx->prm.box); ++ctx->launches; }
+                                                                  ctx->prm.box, slot); ++ctx->launches; }
   else
     { k_drift<float><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>(pos, (const float*)mom, ctx->n, factor,
-                                                                 ctx->prm.box); ++ctx->launches; }
-  ctx->pairs_built = false;  // positions moved: the tiling must be rebuilt
-  ctx->sorted = false;
-  ctx->sorted_pos = nullptr;
+                                                                 ctx->prm.box, slot); ++ctx->launches; }
   return cuda_check(ctx, cudaGetLastError(), "drift kernel");
 }
 

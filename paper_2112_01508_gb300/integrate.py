@@ -31,7 +31,7 @@ def substep_rung_min(k: int, n_rung: int) -> int:
 
 def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: float, eta: float, eps: float,
                   n_steps: int, precision: int = 32, period: int | None = None, carry=(),
-                  history: list | None = None, on_substep=None, long_range=None):
+                  history: list | None = None, on_substep=None, long_range=None, resort_every: int = 1):
     """Advance (pos, mom) by n_steps global steps of size dt, synchronising after
     every `period` steps (default: once, at the end).
 
@@ -41,9 +41,14 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
     dt / 2^(l+1).  pos (3, n) float64 and mom (3, n) float64/float32 are
     reordered in place by the sorts; `carry` lists further per-particle
     tensors to reorder alongside (for example identifiers).  `on_substep(k,
-    rung_min)` is called after each substep's kick is enqueued.  Returns
-    (rung, kick_state) in the final order.
+    rung_min)` is called after each substep's kick is enqueued.  The particles
+    are sorted again every `resort_every` substeps (1..64; the paper reapplies
+    its memory ordering periodically): in between, the library traverses the
+    drifted positions with its reach widened by the drift since the sort.
+    Returns (rung, kick_state) in the final order.
     """
+    if not 1 <= int(resort_every) <= 64:
+        raise ValueError("resort_every must be in 1..64")
     n_rung = sr.n_rung
     sub = 2 ** (n_rung - 1)
     period = n_steps if period is None else period
@@ -70,7 +75,8 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
         for s in range(1, sub + 1):
             k += 1
             sr.drift(pos, mom, dt / sub)
-            sr.sort(pos, carry=carried)
+            if k % resort_every == 0:
+                sr.sort(pos, carry=carried)
             lmin = substep_rung_min(k, n_rung)
             sr.build_pairs(rung, lmin)
             sr.forces(pos, precision, acc)

@@ -26,8 +26,9 @@ def _dt_for_rungs(pos, eta, eps):
     return 2.0 * float(np.sqrt(2 * eta * eps / np.median(a)))
 
 
-@pytest.mark.parametrize("n_rung,n_steps,period", [(4, 2, None), (3, 3, None), (4, 4, 2)])
-def test_rung_leapfrog_vs_oracle(n_rung, n_steps, period):
+@pytest.mark.parametrize("n_rung,n_steps,period,resort", [(4, 2, None, 1), (3, 3, None, 1), (4, 4, 2, 1),
+                                                         (4, 2, None, 4), (3, 3, 2, 3)])
+def test_rung_leapfrog_vs_oracle(n_rung, n_steps, period, resort):
     n, eta, eps = 4096, 0.025, W.eps
     pos = _subset(n, 5)
     dt = _dt_for_rungs(pos, eta, eps)
@@ -43,7 +44,7 @@ def test_rung_leapfrog_vs_oracle(n_rung, n_steps, period):
         ids = torch.arange(n, dtype=torch.int32, device=dev)
         hist = []
         rung, state = rung_leapfrog(sr, p, q, dt, eta, eps, n_steps, precision=64, period=period, carry=(ids,),
-                                    history=hist)
+                                    history=hist, resort_every=resort)
         sr.sync()
         order = ids.cpu().numpy().astype(np.int64)
         got_p = np.empty_like(pos)
