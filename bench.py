@@ -368,28 +368,32 @@ def run_ours(args):
                                   "substep_ms": statistics.mean(ts), "force_kernel_ms": statistics.mean(tk)}
     # one global step of the full rung cycle (2^(n_rung-1) substeps, synchronised at its end)
     from paper_2112_01508_gb300.integrate import rung_leapfrog
-    cyc = {}
-    for run in ("timed", "counted"):
-        pc, qc = pos0.clone(), torch.zeros_like(mom)
-        cyc_pairs = [0]
 
-        def count(k, lmin):
-            cyc_pairs[0] += sr.stats().pairs_last
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rung_leapfrog(sr, pc, qc, dt, eta, w.eps, 1, precision=32,
-                      on_substep=count if run == "counted" else None)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        cyc[run] = (e0.elapsed_time(e1), cyc_pairs[0])
-    del pc, qc
-    rung_cycle = {"value": cyc["counted"][1] / (cyc["timed"][0] * 1e-3), "unit": UNIT,
-                  "ms_per_global_step": cyc["timed"][0], "substeps": 2 ** (n_rung - 1),
-                  "pairs_per_global_step": cyc["counted"][1],
-                  "note": "fake kick + 128 substeps (drift, sort, work list, FP32 forces of due rungs, rung kick)"}
+    def one_cycle(resort_every):
+        cyc = {}
+        for run in ("timed", "counted"):
+            pc, qc = pos0.clone(), torch.zeros_like(mom)
+            cyc_pairs = [0]
+
+            def count(k, lmin):
+                cyc_pairs[0] += sr.stats().pairs_last
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rung_leapfrog(sr, pc, qc, dt, eta, w.eps, 1, precision=32, resort_every=resort_every,
+                          on_substep=count if run == "counted" else None)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cyc[run] = (e0.elapsed_time(e1), cyc_pairs[0])
+        return {"value": cyc["counted"][1] / (cyc["timed"][0] * 1e-3), "unit": UNIT,
+                "ms_per_global_step": cyc["timed"][0], "substeps": 2 ** (n_rung - 1),
+                "pairs_per_global_step": cyc["counted"][1], "resort_every": resort_every}
+
+    rung_cycle = one_cycle(1)
+    rung_cycle["note"] = "fake kick + 128 substeps (drift, sort, work list, FP32 forces of due rungs, rung kick)"
+    rung_cycle["periodic_resort"] = [one_cycle(k) for k in (4, 16)]
     # subtiles per tile (Section 2.1.3 "Subtiles"; the paper compares fixed 1^3 ... 9^3)
     sweep = {}
     pos_s = pos.clone()
