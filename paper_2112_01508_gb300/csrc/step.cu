@@ -66,11 +66,12 @@ __global__ void k_drift(double* __restrict__ pos, const M* __restrict__ mom, int
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float my = 0.0f;
   if (i < n) {
-    double q2 = 0.0;
+    float q2 = 0.0f;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double q = (double)mom[d * n + i];
-      q2 = fma(q, q, q2);
+      const float qf = (float)q;
+      q2 = fmaf(qf, qf, q2);
       double v = __dadd_rn(pos[d * n + i], __dmul_rn(q, factor));
       const long long vb = __double_as_longlong(v);
       if (!(vb >= 0 && vb < __double_as_longlong(box))) {  // v - L floor(v / L); floor is 0 inside the box
@@ -79,8 +80,9 @@ __global__ void k_drift(double* __restrict__ pos, const M* __restrict__ mom, int
       }
       pos[d * n + i] = v;
     }
-    my = (float)(sqrt(q2) * fabs(factor) * (1.0 + 1e-6));
-    if (!(my < 3.0e38f)) my = 3.0e38f;  // non-finite momenta: the bound saturates
+    // FP32 with a relative margin far above its rounding (a few ulps)
+    my = sqrtf(q2) * (float)fabs(factor) * 1.0001f;
+    if (!(my < 3.0e38f)) my = 3.0e38f;  // non-finite or huge momenta: the bound saturates
   }
   if (disp) {
     const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(my));
