@@ -3,6 +3,7 @@
 // elementwise and HBM-bound; the arithmetic is IEEE double with explicit
 // round-to-nearest intrinsics so that the integer rung decision and the
 // updated momenta/positions are reproducible bit for bit.
+#include <algorithm>
 #include <cmath>
 
 #include "ctx.cuh"
@@ -59,13 +60,14 @@ __global__ void k_kick(M* __restrict__ mom, const A* __restrict__ acc, const int
 }
 
 // disp (optional): receives, by atomic max, an upper bound of the largest
-// displacement |q| |factor| of this drift (non-negative floats order as integers).
+// displacement |q| |factor| of this drift (non-negative floats order as
+// integers).  Grid-stride, one atomic per block.
 template <class M>
-__global__ void k_drift(double* __restrict__ pos, const M* __restrict__ mom, int64_t n, double factor, double box,
-                        float* __restrict__ disp) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_drift(double* __restrict__ pos, const M* __restrict__ mom, int64_t n,
+                                               double factor, double box, float* __restrict__ disp) {
+  __shared__ unsigned warp_max[8];
   float my = 0.0f;
-  if (i < n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float q2 = 0.0f;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -81,12 +83,19 @@ __global__ void k_drift(double* __restrict__ pos, const M* __restrict__ mom, int
       pos[d * n + i] = v;
     }
     // FP32 with a relative margin far above its rounding (a few ulps)
-    my = sqrtf(q2) * (float)fabs(factor) * 1.0001f;
-    if (!(my < 3.0e38f)) my = 3.0e38f;  // non-finite or huge momenta: the bound saturates
+    float di = sqrtf(q2) * (float)fabs(factor) * 1.0001f;
+    if (!(di < 3.0e38f)) di = 3.0e38f;  // non-finite or huge momenta: the bound saturates
+    my = fmaxf(my, di);
   }
   if (disp) {
     const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(my));
-    if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned*)disp, m);
+    if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned b = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = max(b, warp_max[w]);
+      if (b) atomicMax((unsigned*)disp, b);
+    }
   }
 }
 
@@ -224,12 +233,13 @@ extern "C" p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom
     }
   }
   const int t = 256;
+  const unsigned b = std::min<unsigned>(blocks_for(ctx->n, t), (unsigned)std::max(ctx->num_sms, 1) * 8u);
   if (mom_precision == 64)
-    { k_drift<double><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>(pos, (const double*)mom, ctx->n, factor,
-                                                                  ctx->prm.box, slot); ++ctx->launches; }
+    { k_drift<double><<<b, t, 0, ctx->stream>>>(pos, (const double*)mom, ctx->n, factor, ctx->prm.box, slot);
+      ++ctx->launches; }
   else
-    { k_drift<float><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>(pos, (const float*)mom, ctx->n, factor,
-                                                                 ctx->prm.box, slot); ++ctx->launches; }
+    { k_drift<float><<<b, t, 0, ctx->stream>>>(pos, (const float*)mom, ctx->n, factor, ctx->prm.box, slot);
+      ++ctx->launches; }
   return cuda_check(ctx, cudaGetLastError(), "drift kernel");
 }
 
