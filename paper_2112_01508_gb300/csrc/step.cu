@@ -61,7 +61,7 @@ __global__ void k_kick(M* __restrict__ mom, const A* __restrict__ acc, const int
 
 // disp (optional): receives, by atomic max, an upper bound of the largest
 // displacement |q| |factor| of this drift (non-negative floats order as
-// integers).  Grid-stride, one atomic per block.
+// integers), one atomic per block.
 template <class M>
 __global__ void __launch_bounds__(256) k_drift(double* __restrict__ pos, const M* __restrict__ mom, int64_t n,
                                                double factor, double box, float* __restrict__ disp) {
@@ -233,7 +233,7 @@ extern "C" p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom
     }
   }
   const int t = 256;
-  const unsigned b = std::min<unsigned>(blocks_for(ctx->n, t), (unsigned)std::max(ctx->num_sms, 1) * 8u);
+  const unsigned b = blocks_for(ctx->n, t);
   if (mom_precision == 64)
     { k_drift<double><<<b, t, 0, ctx->stream>>>(pos, (const double*)mom, ctx->n, factor, ctx->prm.box, slot);
       ++ctx->launches; }
