@@ -124,3 +124,38 @@ def test_rung_leapfrog_with_long_range_vs_oracle():
     dp -= np.round(dp)
     assert np.abs(dp).max() <= 1e-10 * W.x_r
     assert np.abs(got_q - q_ref).max() <= 1e-10 * np.abs(q_ref).max()
+
+
+@pytest.mark.parametrize("mom_dt,acc_dt", [(np.float64, np.float64), (np.float64, np.float32),
+                                           (np.float32, np.float32), (np.float32, np.float64)])
+@pytest.mark.parametrize("k,sync", [(1, False), (2, False), (4, False), (6, False), (8, True)])
+def test_rung_kick_bitexact(mom_dt, acc_dt, k, sync):
+    """One rung kick against the oracle's: momenta (rounded once to FP32 where stored
+    in FP32), rungs and kick states bit for bit, jumps in both directions included."""
+    n, n_rung, dt, eta, eps = 50000, 4, 0.07, 0.025, W.eps
+    rng = np.random.default_rng(k)
+    mag = np.exp(rng.uniform(np.log(1e-3), np.log(1e5), n))
+    acc = rng.normal(size=(3, n))
+    acc = (acc * mag / np.linalg.norm(acc, axis=0)).astype(acc_dt)
+    mom = rng.normal(size=(3, n)).astype(mom_dt)
+    rung = rng.integers(0, n_rung, n).astype(np.int8)
+    state = rng.integers(0, 3, n).astype(np.int8)
+    tz = 0
+    while tz < n_rung - 1 and (k >> tz) & 1 == 0:
+        tz += 1
+    lmin = n_rung - 1 - tz
+    q_ref = mom.astype(np.float64).copy()
+    r_ref, s_ref = rung.copy(), state.copy()
+    oracle.rung_kick(q_ref, acc.astype(np.float64), r_ref, s_ref, lmin, k, n_rung, dt, eta, eps, sync)
+    with ShortRange(n, W.x_s, W.x_r, W.G_m, softening="bspline", eps=eps, n_rung=n_rung) as sr:
+        q = torch.from_numpy(mom.copy()).cuda()
+        r = torch.from_numpy(rung.copy()).cuda()
+        s = torch.from_numpy(state.copy()).cuda()
+        sr.rung_kick(q, torch.from_numpy(acc).cuda(), r, s, lmin, k, dt, eta, eps, synchronize=sync)
+        sr.sync()
+        got_q, got_r, got_s = q.cpu().numpy(), r.cpu().numpy(), s.cpu().numpy()
+    np.testing.assert_array_equal(got_q, q_ref.astype(mom_dt))
+    np.testing.assert_array_equal(got_r, r_ref)
+    np.testing.assert_array_equal(got_s, s_ref)
+    if not sync:
+        assert (got_r != rung).any()  # some particles jumped
