@@ -31,6 +31,8 @@
  *   - "precision" arguments are 32 (float) or 64 (double).
  *   - After p3m_sr_sort, every other call assumes the particles are in the
  *     sorted (tile -> subtile -> particle) order and positions lie in [0, L).
+ *     p3m_sr_drift may move the sorted positions without invalidating the sort
+ *     (up to 64 drifts; see p3m_sr_drift).
  */
 #ifndef P3M_SR_H
 #define P3M_SR_H
@@ -49,7 +51,8 @@ typedef enum {
   P3M_ERR_CUDA = 4,           /* a CUDA runtime call failed                         */
   P3M_ERR_TIMEOUT = 5,        /* reserved: a bounded device-side wait expired       */
   P3M_ERR_NONFINITE = 6,      /* non-finite or out-of-box input met by a kernel     */
-  P3M_ERR_STATE = 7           /* call out of order (e.g. forces before sort)        */
+  P3M_ERR_STATE = 7           /* call out of order (e.g. forces before sort), or
+                                 positions drifted too far since the sort          */
 } p3m_status;
 
 typedef enum { P3M_SOFT_NONE = 0, P3M_SOFT_PLUMMER = 1, P3M_SOFT_BSPLINE = 2 } p3m_softening;
