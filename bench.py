@@ -173,10 +173,10 @@ def cpu_oracle_rate(w, pos, n_recv: int, seed: int = 7):
     return float(pairs.sum()) / dt, dt, int(pairs.sum()), len(recv), oracle.num_threads()
 
 
-def traffic_from_profiles():
+def traffic_from_profiles(workload: str):
     """DRAM traffic of the pair kernel from the committed ncu summary, if it was
-    captured on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "force_f32_n2m.json")
+    captured on this workload and the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", f"force_f32_{workload}.json")
     if not os.path.exists(p):
         return None
     try:
@@ -277,7 +277,7 @@ def run_ours(args):
     achieved = pairs_avg / (kern_avg_ms * 1e-3)
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / OPS_PER_PAIR
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": traffic_from_profiles(),
+                "frac": achieved / peak, "traffic": traffic_from_profiles(w.name),
                 "kernel": "k_force_packed<bspline> (FP32 forward)", "kernel_ms": kern_avg_ms,
                 "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz / "
                               f"{OPS_PER_PAIR} FP32 ops per pair"}
