@@ -347,6 +347,29 @@ def run_ours(args):
                 "mesh_bytes": st_pm.mesh_bytes, "fft_work_bytes": st_pm.fft_work_bytes}
     long_range["fp32_vs_fp64_rel_rms"] = float(torch.sqrt(((lr32.double() - lr64) ** 2).sum() / (lr64 ** 2).sum()))
     del lr32, lr64
+    # the differentiable path: 16 KDK steps with checkpoints every 4 (FP32 forces), then
+    # the backward pass (recomputed segments + the adjoint kernel); rung-0 step of Eq. rung
+    from paper_2112_01508_gb300.autograd import leapfrog
+    dt_lf = (2.0 * eta * w.eps / max(q99, 1e-30)) ** 0.5
+    x0 = pos0.clone().requires_grad_(True)
+    wts = torch.randn((3, n), dtype=torch.float64, device=dev)
+    lf = []
+    for _ in range(2):
+        x0.grad = None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x16, _ = leapfrog(x0, torch.zeros_like(pos0), sr, dt_lf, 16, 4, precision=32)
+        e1.record(stream)
+        (x16 * wts).sum().backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        lf.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+    differentiable = {"steps": 16, "checkpoint_every": 4, "precision": "fp32 forces and adjoint",
+                      "forward_ms": lf[-1][0], "backward_ms": lf[-1][1],
+                      "backward_over_forward": lf[-1][1] / lf[-1][0]}
+    del x0, x16, wts
     # substeps of the rung cycle on this state's rungs: receivers l >= l_cur (Section 2.2.2)
     rung_substeps = {}
     for lc in range(n_rung):
@@ -516,6 +539,7 @@ def run_ours(args):
             "tabulated_2p12": tabulated,
             "n_sub_sweep_force_ms": sweep,
             "long_range_pm": long_range,
+            "differentiable_leapfrog": differentiable,
             "subtile_refinement": refinement,
             "rung_substeps": rung_substeps,
             "rung_cycle": rung_cycle,
