@@ -7,6 +7,7 @@ import oracle
 import synth
 from paper_2112_01508_gb300 import ShortRange
 from paper_2112_01508_gb300.integrate import rung_leapfrog, substep_rung_min
+from tests._gpu_helpers import rel_rms
 
 pytestmark = pytest.mark.gpu
 
@@ -159,3 +160,32 @@ def test_rung_kick_bitexact(mom_dt, acc_dt, k, sync):
     np.testing.assert_array_equal(got_s, s_ref)
     if not sync:
         assert (got_r != rung).any()  # some particles jumped
+
+
+def test_rung_leapfrog_fp32_momenta_vs_oracle():
+    """FP32 momenta (stored once rounded after each FP64 kick) and FP32 forces: the
+    cycle stays within FP32 rounding of the FP64 oracle cycle."""
+    n, eta, eps, n_rung, n_steps = 4096, 0.025, W.eps, 4, 2
+    pos = _subset(n, 11)
+    dt = _dt_for_rungs(pos, eta, eps)
+    p_ref, q_ref, rung_ref, _, _ = oracle.rung_leapfrog(
+        pos, np.zeros_like(pos), W.x_s, W.x_r, W.G_m, "bspline", eps, dt, eta, n_rung, n_steps)
+    dev = torch.device("cuda")
+    with ShortRange(n, W.x_s, W.x_r, W.G_m, softening="bspline", eps=eps, n_sub=W.n_sub, n_rung=n_rung) as sr:
+        p = torch.from_numpy(pos.copy()).to(dev)
+        q = torch.zeros((3, n), dtype=torch.float32, device=dev)
+        ids = torch.arange(n, dtype=torch.int32, device=dev)
+        rung, _ = rung_leapfrog(sr, p, q, dt, eta, eps, n_steps, precision=32, carry=(ids,), resort_every=2)
+        sr.sync()
+        order = ids.cpu().numpy().astype(np.int64)
+        got_p = np.empty_like(pos)
+        got_q = np.empty_like(pos)
+        got_p[:, order] = p.cpu().numpy()
+        got_q[:, order] = q.double().cpu().numpy()
+        got_rung = np.empty(n, np.int8)
+        got_rung[order] = rung.cpu().numpy()
+    assert (got_rung == rung_ref).mean() > 0.999
+    dp = got_p - p_ref
+    dp -= np.round(dp)
+    assert np.abs(dp).max() <= 1e-6 * W.x_r
+    assert rel_rms(got_q, q_ref) <= 1e-5

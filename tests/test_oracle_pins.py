@@ -472,3 +472,38 @@ def test_rung_leapfrog_with_long_range_is_kdk_of_the_total_force():
             q = oracle.kick(q, pm.lr_accel(x, n_phi, XS, GM), [dt / 2])
     np.testing.assert_array_equal(p1, x)
     np.testing.assert_array_equal(q1, q)
+
+
+def test_rung_jump_rules():
+    """The time-stepping figure's jump rules: up by one rung at any kick (next kick
+    1/2 of the finer rung's), down by one rung only at every other kick of the rung
+    (next kick 3/4 of the coarser rung's)."""
+    n_rung, dt, eta, eps = 4, 0.1, 0.025, 0.01
+    q2 = (dt * dt / (2 * eta * eps)) ** 2
+    big = np.sqrt(16.0 ** 3 * 4 / q2)      # Eq. rung gives rung 3 for |a| = big
+    for k in range(1, 9):
+        tz = 0
+        while tz < n_rung - 1 and (k >> tz) & 1 == 0:
+            tz += 1
+        lmin = n_rung - 1 - tz
+        for l in range(lmin, n_rung):
+            for a_mag, want_dir in ((0.0, -1), (big, +1)):
+                acc = np.zeros((3, 1))
+                acc[0, 0] = a_mag
+                mom = np.zeros((3, 1))
+                rung = np.array([l], np.int8)
+                state = np.array([0], np.int8)
+                oracle.rung_kick(mom, acc, rung, state, lmin, k, n_rung, dt, eta, eps, False)
+                if want_dir < 0:
+                    odd = (k >> (n_rung - 1 - l)) & 1
+                    if l > 0 and odd:
+                        assert rung[0] == l - 1 and state[0] == 2
+                    else:
+                        assert rung[0] == l and state[0] == 0
+                else:
+                    if l < n_rung - 1:
+                        assert rung[0] == l + 1 and state[0] == 1   # one rung at a time
+                    else:
+                        assert rung[0] == l and state[0] == 0
+                # the kick itself used the rung held before the jump
+                assert mom[0, 0] == pytest.approx(a_mag * dt / 2 ** l, rel=1e-15, abs=0)
