@@ -164,28 +164,38 @@ def test_rung_kick_bitexact(mom_dt, acc_dt, k, sync):
 
 def test_rung_leapfrog_fp32_momenta_vs_oracle():
     """FP32 momenta (stored once rounded after each FP64 kick) and FP32 forces: the
-    cycle stays within FP32 rounding of the FP64 oracle cycle."""
+    cycle stays within FP32 rounding of the FP64 oracle cycle.  A particle whose
+    acceleration sits within FP32 rounding of a rung boundary may take another rung
+    (and kick schedule): such particles are counted, not compared."""
     n, eta, eps, n_rung, n_steps = 4096, 0.025, W.eps, 4, 2
     pos = _subset(n, 11)
     dt = _dt_for_rungs(pos, eta, eps)
-    p_ref, q_ref, rung_ref, _, _ = oracle.rung_leapfrog(
+    p_ref, q_ref, _, _, hist_ref = oracle.rung_leapfrog(
         pos, np.zeros_like(pos), W.x_s, W.x_r, W.G_m, "bspline", eps, dt, eta, n_rung, n_steps)
     dev = torch.device("cuda")
     with ShortRange(n, W.x_s, W.x_r, W.G_m, softening="bspline", eps=eps, n_sub=W.n_sub, n_rung=n_rung) as sr:
         p = torch.from_numpy(pos.copy()).to(dev)
         q = torch.zeros((3, n), dtype=torch.float32, device=dev)
         ids = torch.arange(n, dtype=torch.int32, device=dev)
-        rung, _ = rung_leapfrog(sr, p, q, dt, eta, eps, n_steps, precision=32, carry=(ids,), resort_every=2)
+        hist = []
+        rung_leapfrog(sr, p, q, dt, eta, eps, n_steps, precision=32, carry=(ids,), resort_every=2, history=hist)
         sr.sync()
         order = ids.cpu().numpy().astype(np.int64)
         got_p = np.empty_like(pos)
         got_q = np.empty_like(pos)
         got_p[:, order] = p.cpu().numpy()
         got_q[:, order] = q.double().cpu().numpy()
-        got_rung = np.empty(n, np.int8)
-        got_rung[order] = rung.cpu().numpy()
-    assert (got_rung == rung_ref).mean() > 0.999
-    dp = got_p - p_ref
+    # rung histories in the caller's order (the GPU history rows follow the sorted order
+    # of their substep, so compare the multiset per substep and the final order exactly)
+    same = np.ones(n, bool)
+    last = np.empty(n, np.int8)
+    last[order] = hist[-1].cpu().numpy()
+    same &= last == hist_ref[-1]
+    for h_gpu, h_ref in zip(hist, hist_ref):
+        assert abs(np.bincount(h_gpu.cpu().numpy(), minlength=n_rung) - np.bincount(h_ref, minlength=n_rung)).max() \
+            <= 4
+    assert same.mean() > 0.999
+    dp = (got_p - p_ref)[:, same]
     dp -= np.round(dp)
     assert np.abs(dp).max() <= 1e-6 * W.x_r
-    assert rel_rms(got_q, q_ref) <= 1e-5
+    assert rel_rms(got_q[:, same], q_ref[:, same]) <= 1e-5
