@@ -39,7 +39,8 @@ UNIT = "pair-interactions/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-OPS_PER_PAIR = 26  # FP32 pipe instructions per interacting pair fixed for the roofline
+OPS_PER_PAIR = 26  # FP32 pipe instructions per interacting pair, one-sided (gathering) kernel
+OPS_PER_PAIR_SYM = 29  # per unordered pair in the Newton-III kernel: the same 26 + 3 for the partner's sum
 
 
 def parse_args():
@@ -52,7 +53,8 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 18, help="receivers in the CPU-oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1 << 14, help="receivers per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["forces32", "forces64", "vjp32", "sort", "pm32"], default=None,
+    ap.add_argument("--only", choices=["forces32", "forces32_gather", "forces64", "vjp32", "sort", "pm32"],
+                    default=None,
                     help="profiling mode: run just one kernel family (no contract line)")
     return ap.parse_args()
 
@@ -275,12 +277,15 @@ def run_ours(args):
     kern_avg_ms = statistics.mean(kern_ms)
     pairs_avg = statistics.mean(pairs)
     achieved = pairs_avg / (kern_avg_ms * 1e-3)
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / OPS_PER_PAIR
+    lane_rate = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    # the all-active step runs the Newton-III kernel: one evaluation serves two ordered interactions
+    peak = 2.0 * lane_rate / OPS_PER_PAIR_SYM
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
                 "frac": achieved / peak, "traffic": traffic_from_profiles(w.name),
-                "kernel": "k_force_packed<bspline> (FP32 forward)", "kernel_ms": kern_avg_ms,
+                "kernel": "k_force_sym<bspline> (FP32 forward, each pair once)", "kernel_ms": kern_avg_ms,
                 "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz / "
-                              f"{OPS_PER_PAIR} FP32 ops per pair"}
+                              f"{OPS_PER_PAIR_SYM} FP32 ops per unordered pair x 2 ordered interactions",
+                "frac_of_one_sided_peak": achieved / (lane_rate / OPS_PER_PAIR)}
 
     # FP64 path and adjoint on the same (current) particle state
     sr.sort(pos, carry=[mom, rung])
@@ -302,6 +307,20 @@ def run_ours(args):
         vjp_ms.append(sr.stats().vjp_kernel_ms)
     a32 = acc.double()
     parity_32_64 = float(torch.sqrt(((a32 - acc64) ** 2).sum() / (acc64 ** 2).sum()))
+    # the one-sided (gathering) FP32 kernel on the same state: each pair from both sides
+    sr.set_symmetric(False)
+    gat_ms = []
+    acc_g = torch.zeros_like(acc)
+    for _ in range(3):
+        flush.zero_()
+        sr.forces(pos, 32, acc_g)
+        gat_ms.append(sr.stats().force_kernel_ms)
+    sr.set_symmetric(True)
+    gat_rate = sr.stats().pairs_last / (statistics.mean(gat_ms) * 1e-3)
+    one_sided = {"value": gat_rate, "unit": UNIT, "kernel_ms": statistics.mean(gat_ms),
+                 "kernel": "k_force_packed<bspline>", "frac_of_one_sided_peak": gat_rate / (lane_rate / OPS_PER_PAIR),
+                 "rel_rms_vs_symmetric": float(torch.sqrt(((acc_g.double() - a32) ** 2).sum() / (a32 ** 2).sum()))}
+    del acc_g
     fp64_rate = fp64_pairs / (statistics.mean(fp64_ms) * 1e-3)
     # the paper's tabulated bracket (2^12 NGP bins in r^2) on the same state
     tab_ms = []
@@ -380,7 +399,7 @@ def run_ours(args):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             sr.sort(pos, carry=[mom, rung])
-            sr.build_pairs(rung, lc)
+            sr.build_pairs(None if lc == 0 else rung, lc)
             sr.forces(pos, 32, acc)
             sr.kick(mom, acc, [0.0] * n_rung, rung, lc)  # zero kick: timed, state unchanged
             e1.record(stream)
@@ -536,6 +555,8 @@ def run_ours(args):
             "fp32_over_fp64": achieved / fp64_rate,
             "fp32_vs_fp64_rel_rms": parity_32_64,
             "adjoint_over_forward": statistics.mean(vjp_ms) / statistics.mean(fwd_ms),
+            "adjoint_over_one_sided_forward": statistics.mean(vjp_ms) / statistics.mean(gat_ms),
+            "one_sided_fp32": one_sided,
             "tabulated_2p12": tabulated,
             "n_sub_sweep_force_ms": sweep,
             "long_range_pm": long_range,
@@ -587,8 +608,10 @@ def run_only(args):
         print(json.dumps({"only": args.only, "workload": w.name, "mesh_ms": times, "n_phi": w.n_phi}))
         sr.close()
         return
+    if args.only == "forces32_gather":
+        sr.set_symmetric(False)
     for k in range(args.warmup + args.steps):
-        if args.only == "forces32":
+        if args.only in ("forces32", "forces32_gather"):
             sr.forces(pos, 32, acc32)
         elif args.only == "forces64":
             sr.forces(pos, 64, acc64)

@@ -192,8 +192,25 @@ p3m_status p3m_sr_build_pairs(p3m_sr_ctx* ctx, const int8_t* rung, int rung_min)
  *              double.
  *   acc_out    receivers' rows are overwritten; other rows are untouched.
  * The FP32 path requires x_r <= 4.6 x_s (range of its erfc fit).
+ * With every particle a receiver (build_pairs with rung NULL) the FP32 path
+ * evaluates each pair once and updates both particles (see
+ * p3m_sr_set_symmetric); its sums are then added with atomics, so the last
+ * bits of the result depend on the order of execution.
  */
 p3m_status p3m_sr_forces(p3m_sr_ctx* ctx, const double* pos, int precision, void* acc_out);
+
+/*
+ * Pair evaluation of the all-active FP32 forces.  enable = 1 (the default):
+ * each unordered pair {i, j} is evaluated once and both particles receive their
+ * share, as the paper's tile pairing does (Section 2.1.3: a supplier tile is
+ * never paired again with a receiver tile it already met in the opposite
+ * roles); the per-particle sums are FP32 atomics into a context buffer.
+ * enable = 0: every receiver gathers its own sum over all its partners, each
+ * pair being evaluated from both sides; the result is then bitwise
+ * reproducible.  Partially active sets, the FP64 path, the tabulated variant
+ * and the vjp always gather.  P3M_ERR_INVALID for a NULL context.
+ */
+p3m_status p3m_sr_set_symmetric(p3m_sr_ctx* ctx, int enable);
 
 /*
  * The paper's tabulated variant of the FP32 forces (Section 2.1.3, "Other

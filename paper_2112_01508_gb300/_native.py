@@ -34,7 +34,7 @@ EXPORTS = (
     "p3m_sr_create", "p3m_sr_destroy", "p3m_sr_last_error", "p3m_sr_sync", "p3m_sr_stats", "p3m_sr_sort",
     "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
     "p3m_sr_permute", "p3m_sr_unpermute", "p3m_sr_forces_noalloc", "p3m_sr_forces_tabulated",
-    "p3m_sr_rung_kick", "p3m_sr_set_subtiles",
+    "p3m_sr_rung_kick", "p3m_sr_set_subtiles", "p3m_sr_set_symmetric",
 )
 
 
@@ -128,6 +128,8 @@ def load() -> ctypes.CDLL:
         L.p3m_sr_rung_kick.restype = i
         L.p3m_sr_set_subtiles.argtypes = [p, ctypes.POINTER(i)]
         L.p3m_sr_set_subtiles.restype = i
+        L.p3m_sr_set_symmetric.argtypes = [p, i]
+        L.p3m_sr_set_symmetric.restype = i
         _lib = L
         return L
 
@@ -161,6 +163,10 @@ def p3m_sr_stats(ctx):
 def p3m_sr_set_subtiles(ctx, n_sub) -> int:
     arr = (ctypes.c_int * 3)(*[int(v) for v in n_sub])
     return load().p3m_sr_set_subtiles(ctx, arr)
+
+
+def p3m_sr_set_symmetric(ctx, enable: bool) -> int:
+    return load().p3m_sr_set_symmetric(ctx, 1 if enable else 0)
 
 
 def p3m_sr_sort(ctx, pos_ptr: int, carry_ptrs, carry_bytes, perm_out_ptr, subtile_id_out_ptr) -> int:

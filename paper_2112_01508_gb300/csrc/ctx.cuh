@@ -70,6 +70,7 @@ struct p3m_sr_ctx {
   bool pairs_built = false;
   bool all_chunks_built = false;
   bool all_active = true;
+  bool symmetric = true;               // all-active FP32 forces: each pair once, both updated
 
   std::string last_error;
 };

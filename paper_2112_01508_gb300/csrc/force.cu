@@ -353,6 +353,71 @@ __device__ __forceinline__ void load_chunk(const TraversalArgs& a, const Reach& 
   }
 }
 
+// Candidate subtile cc (of ncand) of the blocky ball around the chunk's subtile
+// block: whether its box gap to the receivers' bounding box is below the reach
+// and it holds particles at indices >= clip_from; if so their range and the
+// subtile offset.
+template <class Real>
+__device__ __forceinline__ bool candidate_range(const TraversalArgs& a, const Reach& rc, const ChunkFrame<Real>& F,
+                                                int cc, int ncand, int clip_from, int& start, int& cnt,
+                                                unsigned& dpk) {
+  const Geometry& g = a.g;
+  start = 0;
+  cnt = 0;
+  dpk = 0;
+  if (cc >= ncand) return false;
+  int dz = cc % F.ext[2];
+  int t = cc / F.ext[2];
+  int dy = t % F.ext[1];
+  int dx = t / F.ext[1];
+  dx += F.elo[0]; dy += F.elo[1]; dz += F.elo[2];
+  const int dd[3] = {dx, dy, dz};
+  const Real blo[3] = {F.lo.x, F.lo.y, F.lo.z}, bhi[3] = {F.hi.x, F.hi.y, F.hi.z};
+  Real gap2 = Real(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Real side;
+    if constexpr (sizeof(Real) == 4) side = g.side32[d]; else side = g.side64[d];
+    Real jlo = F.org[d] + Real(dd[d]) * side;
+    Real jhi = jlo + side;
+    Real gp = fmax(fmax(blo[d] - jhi, jlo - bhi[d]), Real(0));
+    gap2 += gp * gp;
+  }
+  Real sub2;
+  if constexpr (sizeof(Real) == 4) sub2 = rc.sub2; else sub2 = rc.sub2_d;
+  if (!(gap2 < sub2)) return false;
+  int gx = F.g0[0] + dx, gy = F.g0[1] + dy, gz = F.g0[2] + dz;
+  gx += gx < 0 ? g.M[0] : (gx >= g.M[0] ? -g.M[0] : 0);
+  gy += gy < 0 ? g.M[1] : (gy >= g.M[1] ? -g.M[1] : 0);
+  gz += gz < 0 ? g.M[2] : (gz >= g.M[2] ? -g.M[2] : 0);
+  const int sid = encode_subtile(g, gx, gy, gz);
+  start = max(a.offsets[sid], clip_from);
+  cnt = a.offsets[sid + 1] - start;
+  dpk = pack_delta(dx, dy, dz);
+  return cnt > 0;
+}
+
+// Append the taken candidates of one round (ballot tm) to the warp's list.
+__device__ __forceinline__ void append_round(WarpList& L, int lane, bool take, int start, int cnt, unsigned dpk,
+                                             unsigned tm, int& nlist, int& total) {
+  const unsigned full = 0xffffffffu;
+  int v = take ? cnt : 0;  // inclusive scan of the taken counts
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int u = __shfl_up_sync(full, v, o);
+    if (lane >= o) v += u;
+  }
+  const int round_total = __shfl_sync(full, v, 31);
+  if (take) {
+    const int slot = nlist + __popc(tm & ((1u << lane) - 1u));
+    L.start[slot] = start;
+    L.pre[slot] = total + v - cnt;
+    L.delta[slot] = dpk;
+  }
+  nlist += __popc(tm);
+  total += round_total;
+}
+
 // Enumerate the subtiles of the blocky ball around the chunk's subtile block
 // (32 candidates per round, one per lane), keep those whose box gap to the
 // receivers' bounding box is below x_r and that hold particles, and append their
@@ -361,75 +426,64 @@ template <class Real, class Proc>
 __device__ __forceinline__ void enumerate_suppliers(const TraversalArgs& a, const Reach& rc, const ChunkFrame<Real>& F,
                                                     WarpList& L, int lane, Proc&& proc) {
   const unsigned full = 0xffffffffu;
-  const Geometry& g = a.g;
   const int ncand = F.ext[0] * F.ext[1] * F.ext[2];
   int nlist = 0, total = 0;
   for (int cb = 0; cb < ncand; cb += kWarp) {
-    int cc = cb + lane;
-    bool take = false;
-    int start = 0, cnt = 0;
-    unsigned dpk = 0;
-    if (cc < ncand) {
-      int dz = cc % F.ext[2];
-      int t = cc / F.ext[2];
-      int dy = t % F.ext[1];
-      int dx = t / F.ext[1];
-      dx += F.elo[0]; dy += F.elo[1]; dz += F.elo[2];
-      const int dd[3] = {dx, dy, dz};
-      const Real blo[3] = {F.lo.x, F.lo.y, F.lo.z}, bhi[3] = {F.hi.x, F.hi.y, F.hi.z};
-      Real gap2 = Real(0);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        Real side;
-        if constexpr (sizeof(Real) == 4) side = g.side32[d]; else side = g.side64[d];
-        Real jlo = F.org[d] + Real(dd[d]) * side;
-        Real jhi = jlo + side;
-        Real gp = fmax(fmax(blo[d] - jhi, jlo - bhi[d]), Real(0));
-        gap2 += gp * gp;
-      }
-      Real sub2;
-      if constexpr (sizeof(Real) == 4) sub2 = rc.sub2; else sub2 = rc.sub2_d;
-      if (gap2 < sub2) {
-        int gx = F.g0[0] + dx, gy = F.g0[1] + dy, gz = F.g0[2] + dz;
-        gx += gx < 0 ? g.M[0] : (gx >= g.M[0] ? -g.M[0] : 0);
-        gy += gy < 0 ? g.M[1] : (gy >= g.M[1] ? -g.M[1] : 0);
-        gz += gz < 0 ? g.M[2] : (gz >= g.M[2] ? -g.M[2] : 0);
-        int sid = encode_subtile(g, gx, gy, gz);
-        start = a.offsets[sid];
-        cnt = a.offsets[sid + 1] - start;
-        take = cnt > 0;
-        dpk = pack_delta(dx, dy, dz);
-      }
-    }
-    unsigned tm = __ballot_sync(full, take);
-    int ntake = __popc(tm);
-    if (ntake == 0) continue;
-    if (nlist + ntake > kListCap) {
+    int start, cnt;
+    unsigned dpk;
+    const bool take = candidate_range<Real>(a, rc, F, cb + lane, ncand, 0, start, cnt, dpk);
+    const unsigned tm = __ballot_sync(full, take);
+    if (tm == 0) continue;
+    if (nlist + __popc(tm) > kListCap) {
       __syncwarp();
       proc(nlist, total);
       __syncwarp();
       nlist = 0;
       total = 0;
     }
-    int v = take ? cnt : 0;  // inclusive scan of the taken counts
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int u = __shfl_up_sync(full, v, o);
-      if (lane >= o) v += u;
-    }
-    int round_total = __shfl_sync(full, v, 31);
-    if (take) {
-      int slot = nlist + __popc(tm & ((1u << lane) - 1u));
-      L.start[slot] = start;
-      L.pre[slot] = total + v - cnt;
-      L.delta[slot] = dpk;
-    }
-    nlist += ntake;
-    total += round_total;
+    append_round(L, lane, take, start, cnt, dpk, tm, nlist, total);
   }
   __syncwarp();
   if (nlist > 0) proc(nlist, total);
   __syncwarp();
+}
+
+// As enumerate_suppliers, with the ranges cut to indices >= clip_from, and
+// `proc(nlist, total, last)` called from one place: each time the list fills up
+// and once more at the end (last = true, possibly with an empty list), so that
+// a large consumer is inlined once.
+template <class Real, class Proc>
+__device__ __forceinline__ void enumerate_suppliers_once(const TraversalArgs& a, const Reach& rc,
+                                                         const ChunkFrame<Real>& F, WarpList& L, int lane,
+                                                         int clip_from, Proc&& proc) {
+  const unsigned full = 0xffffffffu;
+  const int ncand = F.ext[0] * F.ext[1] * F.ext[2];
+  int nlist = 0, total = 0;
+  int cb = 0;
+  bool take = false;
+  int start = 0, cnt = 0;
+  unsigned dpk = 0, tm = 0;
+  for (;;) {
+    bool overflow = false;
+    for (; cb < ncand; cb += kWarp) {
+      take = candidate_range<Real>(a, rc, F, cb + lane, ncand, clip_from, start, cnt, dpk);
+      tm = __ballot_sync(full, take);
+      if (tm == 0) continue;
+      if (nlist + __popc(tm) > kListCap) {  // flush first; this round is appended after
+        overflow = true;
+        break;
+      }
+      append_round(L, lane, take, start, cnt, dpk, tm, nlist, total);
+    }
+    __syncwarp();
+    proc(nlist, total, !overflow);
+    __syncwarp();
+    if (!overflow) break;
+    nlist = 0;
+    total = 0;
+    append_round(L, lane, take, start, cnt, dpk, tm, nlist, total);
+    cb += kWarp;
+  }
 }
 
 // Load supplier number f of the list (lane-parallel): its position in the
@@ -796,6 +850,298 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
 }
 
 // ---------------------------------------------------------------------------
+// FP32 forward with Newton's third law, for calls in which every particle is a
+// receiver.  The paper pairs two neighbouring tiles only once and updates the
+// particles of both (Section 2.1.3); here each unordered pair {i, j} of sorted
+// indices i < j is evaluated once, by the chunk that holds i, and both
+// particles receive their share.  The chunk's supplier ranges are cut to
+// indices >= its first receiver, and suppliers of the chunk itself are masked
+// to j > i.
+//
+// The survivors of the box test are staged 64 at a time as 32 packed pairs.  A
+// block of P pairs (P a power of two <= 32) takes P steps: at step k, lane l
+// evaluates its receiver against pair (l + k) mod P of its group of P lanes, so
+// that every receiver meets every pair once and no two lanes of a group touch
+// one supplier at the same time.  Each pair's accumulator travels with it from
+// lane to lane by warp shuffles; at the end of the block the groups' partial
+// sums are reduced and added, like the receivers' own sums at the end of the
+// chunk, into an FP32 float4 array with vector atomics.  k_sym_finish scales
+// that array into the caller's 3 x n output.
+// ---------------------------------------------------------------------------
+
+constexpr float kSymPad = 1e10f;  // padding supplier at -1e10, invalid receiver at +1e10: finite B, no hit
+
+struct SymSmem {
+  WarpList L;
+  float4 sxy[kWarp];  // pair q: (-x_a, -x_b, -y_a, -y_b) of suppliers a = q and b = q + P
+  float2 sz[kWarp];   // (-z_a, -z_b)
+  int2 sj[kWarp];     // (j_a, j_b): sorted indices, -1 for padding
+};
+
+#ifndef P3M_SYM_MINBLOCKS
+#define P3M_SYM_MINBLOCKS 4
+#endif
+
+__device__ __forceinline__ f2 shfl2(f2 v, int src) {
+  f2 r;
+  r.v = __shfl_sync(0xffffffffu, v.v, src);
+  return r;
+}
+__device__ __forceinline__ f2 shfl_xor2(f2 v, int o) {
+  f2 r;
+  r.v = __shfl_xor_sync(0xffffffffu, v.v, o);
+  return r;
+}
+
+template <int SOFT>
+__global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(TraversalArgs a, float4* __restrict__ acc4) {
+  __shared__ SymSmem smem[kPWarps];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  SymSmem& S = smem[threadIdx.x >> 5];
+  float* sxy = (float*)S.sxy;
+  float* szf = (float*)S.sz;
+  int* sjf = (int*)S.sj;
+  const int n_chunks = *a.n_chunks;
+  const Reach rc = make_reach(a);
+  const float xr2 = a.f.xr2_f;
+  const float xr2s = xr2 * kCutScale;
+  unsigned long long pair_total = 0;
+  for (;;) {
+    const int c = next_chunk(a, lane);
+    if (c >= n_chunks) break;
+    const Chunk ch = a.chunks[c];
+    ChunkFrame<float> F;
+    load_chunk<float>(a, rc, ch, lane, F);
+    const int i_self = F.valid ? F.pidx : 0x7fffffff;  // the mask j > i is false on empty lanes
+    const int c_end = ch.start + ch.count;
+    const float rx = F.valid ? F.pi.x : kSymPad, ry = F.valid ? F.pi.y : kSymPad, rz = F.valid ? F.pi.z : kSymPad;
+    const f2 px = pk(rx, rx), py = pk(ry, ry), pz = pk(rz, rz);
+    f2 ax = pk(0.f, 0.f), ay = pk(0.f, 0.f), az = pk(0.f, 0.f);
+    f2 hitsf = pk(0.f, 0.f);
+    int cnt = 0;                          // staged suppliers (warp-uniform)
+    bool blk_near = false, blk_own = false;  // the staged block holds a supplier near the box / of this chunk
+
+    auto stage = [&](int rank, const Vec3<float>& pj, int j) {
+      const int q = rank & (kWarp - 1), h = rank >> 5;
+      sxy[4 * q + h] = -pj.x;
+      sxy[4 * q + 2 + h] = -pj.y;
+      szf[2 * q + h] = -pj.z;
+      sjf[2 * q + h] = j;
+    };
+
+    // Evaluate the staged block of nsup suppliers (1 <= nsup <= 64) against the chunk.
+    auto eval_block = [&](int nsup) {
+      int P = kWarp;
+      if (nsup < 2 * kWarp) {
+        const int half = (nsup + 1) >> 1;
+        P = 1;
+        while (P < half) P <<= 1;
+        // pair q = (supplier q, supplier q + P): move q + P < 32 from the a halves to the b halves
+        if (nsup <= kWarp && lane >= P && lane < nsup) {
+          const int q = lane - P;
+          sxy[4 * q + 1] = sxy[4 * lane];
+          sxy[4 * q + 3] = sxy[4 * lane + 2];
+          szf[2 * q + 1] = szf[2 * lane];
+          sjf[2 * q + 1] = sjf[2 * lane];
+        }
+        if (lane < P && lane + P >= nsup) {
+          sxy[4 * lane + 1] = kSymPad;
+          sxy[4 * lane + 3] = kSymPad;
+          szf[2 * lane + 1] = kSymPad;
+          sjf[2 * lane + 1] = -1;
+        }
+        __syncwarp();
+      }
+      const int qmask = P - 1;
+      const int src = (lane & ~qmask) | ((lane + 1) & qmask);
+      f2 sax = pk(0.f, 0.f), say = pk(0.f, 0.f), saz = pk(0.f, 0.f);
+      int q = lane & qmask;
+      auto run = [&](auto check_soft, auto masked) {
+        constexpr bool kCheckSoft = decltype(check_soft)::value;
+        constexpr bool kMasked = decltype(masked)::value;
+        for (int k = 0; k < P; ++k) {
+          const float4 s = S.sxy[q];
+          const float2 z = S.sz[q];
+          const f2 dx = add2(px, pk(s.x, s.y));
+          const f2 dy = add2(py, pk(s.z, s.w));
+          const f2 dz = add2(pz, pk(z.x, z.y));
+          const f2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, pk(kR2Floor, kR2Floor))));
+          float q0, q1;
+          upk(r2, q0, q1);
+          // No skip of steps without a hit: with 32 different pairs per step
+          // almost every step has one, and the vote costs more than it saves.
+          float c0 = fma_sat(q0, -kCutScale, xr2s), c1 = fma_sat(q1, -kCutScale, xr2s);
+          if (kMasked) {
+            const int2 jj = S.sj[q];
+            c0 = jj.x > i_self ? c0 : 0.f;
+            c1 = jj.y > i_self ? c1 : 0.f;
+          }
+          const f2 cm = pk(c0, c1);
+          hitsf = add2(hitsf, cm);
+          f2 B = bracket_main_f32x2<SOFT>(r2, a.f);
+          // softened branch: a cheap vote first, the exact condition (a hit,
+          // not a zero displacement) only when some pair is that close
+          if (kCheckSoft && __any_sync(full, fminf(q0, q1) < a.f.rsw2_f)) {
+            const bool rare0 = c0 > 0.f && q0 < a.f.rsw2_f && q0 > kR2Self;
+            const bool rare1 = c1 > 0.f && q1 < a.f.rsw2_f && q1 > kR2Self;
+            if (__any_sync(full, rare0 || rare1)) {
+              float b0, b1, Ds;
+              upk(B, b0, b1);
+#pragma unroll 1
+              for (int t = 0; t < 2; ++t) {  // one copy of the softened branch for both halves
+                const float sv = bracket_soft_f32<SOFT, false>(t ? q1 : q0, a.f, a.sc, Ds);
+                if (t == 0 && rare0) b0 = sv;
+                if (t == 1 && rare1) b1 = sv;
+              }
+              B = pk(b0, b1);
+            }
+          }
+          B = mul2(B, cm);
+          ax = fma2(B, dx, ax);
+          ay = fma2(B, dy, ay);
+          az = fma2(B, dz, az);
+          sax = fma2(B, dx, sax);
+          say = fma2(B, dy, say);
+          saz = fma2(B, dz, saz);
+          // the pair of lane l + 1 comes to lane l, with its accumulator
+          sax = shfl2(sax, src);
+          say = shfl2(say, src);
+          saz = shfl2(saz, src);
+          q = (q + 1) & qmask;
+        }
+      };
+      if (blk_near) {
+        if (blk_own) run(std::true_type{}, std::true_type{});
+        else run(std::true_type{}, std::false_type{});
+      } else {
+        if (blk_own) run(std::false_type{}, std::true_type{});
+        else run(std::false_type{}, std::false_type{});
+      }
+      // after P steps lane l holds the sum of its group for pair l mod P
+      for (int o = P; o < kWarp; o <<= 1) {
+        sax = add2(sax, shfl_xor2(sax, o));
+        say = add2(say, shfl_xor2(say, o));
+        saz = add2(saz, shfl_xor2(saz, o));
+      }
+      if (lane < P) {
+        const int2 jj = S.sj[lane];
+        float xa, xb, ya, yb, za, zb;
+        upk(sax, xa, xb);
+        upk(say, ya, yb);
+        upk(saz, za, zb);
+        if (jj.x >= 0) atomicAdd(acc4 + jj.x, make_float4(-xa, -ya, -za, 0.f));
+        if (jj.y >= 0) atomicAdd(acc4 + jj.y, make_float4(-xb, -yb, -zb, 0.f));
+      }
+      __syncwarp();
+    };
+
+    // Stage the survivors of each batch of 32 list positions; evaluate a block
+    // whenever 64 are staged, and the rest once the enumeration is done (one
+    // call site of eval_block, so its loops are inlined once).
+    enumerate_suppliers_once<float>(
+        a, rc, F, S.L, lane, ch.start,
+        [&](int nlist, int total, bool last) {
+          const WarpList& L = S.L;
+          int e_cur = 0;  // list entry holding position b (as in k_force_packed)
+          auto locate = [&](int b, int& j, unsigned& dpk) -> bool {
+            const int ek = e_cur + 1 + lane;
+            const int pos = (ek < nlist) ? L.pre[ek] - b : 64;
+            const unsigned bit = (pos > 0 && pos < kWarp) ? (1u << pos) : 0u;
+            const unsigned starts = __reduce_or_sync(full, bit);
+            const bool at_end = __any_sync(full, pos == kWarp);
+            const unsigned upto = (lane == kWarp - 1) ? 0xffffffffu : ((2u << lane) - 1u);
+            const int e = e_cur + __popc(starts & upto);
+            e_cur += __popc(starts) + (at_end ? 1 : 0);
+            const bool have = b + lane < total;
+            j = have ? L.start[e] + (b + lane - L.pre[e]) : 0;
+            dpk = have ? L.delta[e] : 0u;
+            return have;
+          };
+          int jn;
+          unsigned dn;
+          bool vn = locate(0, jn, dn);
+          float4 rn = vn ? a.rel4[jn] : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int b = 0;; b += kWarp) {
+            const bool more = b < total;  // warp-uniform
+            bool keep = false, near = false, own = false;
+            Vec3<float> pj = {0.f, 0.f, 0.f};
+            int j = 0, rank = 0, ns = 0;
+            if (more) {
+              const bool have = vn;
+              const float4 r = rn;
+              const unsigned dpk = dn;
+              j = jn;
+              vn = (b + kWarp < total) ? locate(b + kWarp, jn, dn) : false;
+              if (vn) rn = a.rel4[jn];
+              if (have) {
+                int ddx, ddy, ddz;
+                unpack_delta(dpk, ddx, ddy, ddz);
+                pj.x = fmaf((float)ddx, a.g.side32[0], r.x);
+                pj.y = fmaf((float)ddy, a.g.side32[1], r.y);
+                pj.z = fmaf((float)ddz, a.g.side32[2], r.z);
+                const float tx = fmaxf(fmaxf(F.lo.x - pj.x, pj.x - F.hi.x), 0.f);
+                const float ty = fmaxf(fmaxf(F.lo.y - pj.y, pj.y - F.hi.y), 0.f);
+                const float tz = fmaxf(fmaxf(F.lo.z - pj.z, pj.z - F.hi.z), 0.f);
+                const float gap2 = fmaf(tx, tx, fmaf(ty, ty, tz * tz));
+                keep = gap2 < a.f.margin2_f;
+                near = keep && gap2 < a.f.rsw2_f;
+              }
+              own = keep && j < c_end;
+              const unsigned m = __ballot_sync(full, keep);
+              ns = __popc(m);
+              rank = cnt + __popc(m & lt_mask);
+              if (keep && rank < 2 * kWarp) stage(rank, pj, j);
+              blk_near = blk_near || __any_sync(full, near && rank < 2 * kWarp);
+              blk_own = blk_own || __any_sync(full, own && rank < 2 * kWarp);
+            }
+            const bool flush = more ? (cnt + ns >= 2 * kWarp) : (last && cnt > 0);
+            if (flush) {
+              __syncwarp();
+              eval_block(more ? 2 * kWarp : cnt);
+              if (more) {
+                blk_near = __any_sync(full, near && rank >= 2 * kWarp);
+                blk_own = __any_sync(full, own && rank >= 2 * kWarp);
+                if (keep && rank >= 2 * kWarp) stage(rank - 2 * kWarp, pj, j);
+                cnt += ns - 2 * kWarp;
+              } else {
+                cnt = 0;
+              }
+            } else {
+              cnt += ns;
+            }
+            if (!more) break;
+          }
+        });
+    float l, h;
+    float4 mine;
+    upk(ax, l, h);
+    mine.x = l + h;
+    upk(ay, l, h);
+    mine.y = l + h;
+    upk(az, l, h);
+    mine.z = l + h;
+    mine.w = 0.f;
+    if (F.valid) atomicAdd(acc4 + F.pidx, mine);
+    upk(hitsf, l, h);
+    const int hits = F.valid ? (int)(l + h) : 0;
+    pair_total += 2ull * (unsigned long long)__reduce_add_sync(full, (unsigned)hits);  // ordered pairs
+  }
+  if (lane == 0 && pair_total) atomicAdd(a.pairs, pair_total);
+}
+
+// acc = -G m * (sum over partners of B(r) (x_i - x_j)), from the float4 sums of k_force_sym.
+__global__ void k_sym_finish(const float4* __restrict__ acc4, int64_t n, float scale, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = acc4[i];
+    out[i] = scale * v.x;
+    out[n + i] = scale * v.y;
+    out[2 * n + i] = scale * v.z;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP32 adjoint, packed broadcast: as k_force_packed, with every particle a
 // receiver and the masked abar of each supplier staged beside its position.
 //   xbar_k = -G m sum_j [ B v + (B'/r) (x_kj . v) x_kj ],  v = abar_k - abar_j.
@@ -988,6 +1334,38 @@ static cudaError_t launch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
   return cudaGetLastError();
 }
 
+// Newton-III FP32 forward (all particles receivers): zero the float4 sums, run
+// k_force_sym, scale the sums into a.out.
+template <int SOFT>
+static cudaError_t launch_sym_soft(p3m_sr_ctx* ctx, const TraversalArgs& a, float4* acc4) {
+  static int blocks_per_sm = 0;
+  if (blocks_per_sm == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_force_sym<SOFT>, kPThreads, 0);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMemsetAsync(acc4, 0, sizeof(float4) * (size_t)ctx->n, s);
+  if (e != cudaSuccess) return e;
+  cudaEventRecord(ctx->kt_ev[0], s);
+  k_force_sym<SOFT><<<(unsigned)(ctx->num_sms * blocks_per_sm), kPThreads, 0, s>>>(a, acc4);
+  ++ctx->launches;
+  cudaEventRecord(ctx->kt_ev[1], s);
+  ctx->kt_pending[0] = true;
+  const unsigned fin = (unsigned)std::min<int64_t>((ctx->n + 255) / 256, (int64_t)ctx->num_sms * 16);
+  k_sym_finish<<<fin, 256, 0, s>>>(acc4, ctx->n, -(float)a.f.G_m, (float*)a.out);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_sym(p3m_sr_ctx* ctx, const TraversalArgs& a) {
+  float4* acc4 = (float4*)ctx->gather_tmp;  // 32 n bytes, idle outside the sort
+  switch (ctx->prm.softening) {
+    case P3M_SOFT_NONE: return launch_sym_soft<P3M_SOFT_NONE>(ctx, a, acc4);
+    case P3M_SOFT_PLUMMER: return launch_sym_soft<P3M_SOFT_PLUMMER>(ctx, a, acc4);
+    default: return launch_sym_soft<P3M_SOFT_BSPLINE>(ctx, a, acc4);
+  }
+}
+
 template <class Real, bool VJP>
 static cudaError_t dispatch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
   switch (ctx->prm.softening) {
@@ -1105,7 +1483,9 @@ extern "C" p3m_status p3m_sr_forces(p3m_sr_ctx* ctx, const double* pos, int prec
   a.counter = ctx->dev_small + 3;
   a.active_idx = ctx->all_active ? nullptr : ctx->active_idx;
   a.out = acc_out;
-  cudaError_t e = (precision == 32) ? dispatch_traverse<float, false>(ctx, a) : dispatch_traverse<double, false>(ctx, a);
+  cudaError_t e;
+  if (precision == 32 && ctx->all_active && ctx->symmetric) e = launch_sym(ctx, a);
+  else e = (precision == 32) ? dispatch_traverse<float, false>(ctx, a) : dispatch_traverse<double, false>(ctx, a);
   if ((st = cuda_check(ctx, e, "force kernel")) != P3M_OK) return st;
   report_latched(ctx);
   return P3M_OK;

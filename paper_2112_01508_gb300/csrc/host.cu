@@ -345,6 +345,12 @@ fail_alloc:
   return st;
 }
 
+extern "C" p3m_status p3m_sr_set_symmetric(p3m_sr_ctx* ctx, int enable) {
+  if (!ctx) return P3M_ERR_INVALID;
+  ctx->symmetric = enable != 0;
+  return P3M_OK;
+}
+
 extern "C" p3m_status p3m_sr_set_subtiles(p3m_sr_ctx* ctx, const int* n_sub) {
   if (!ctx) return P3M_ERR_INVALID;
   if (!n_sub) return fail(ctx, P3M_ERR_INVALID, "set_subtiles: null n_sub");

@@ -78,7 +78,7 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
             if k % resort_every == 0:
                 sr.sort(pos, carry=carried)
             lmin = substep_rung_min(k, n_rung)
-            sr.build_pairs(rung, lmin)
+            sr.build_pairs(None if lmin == 0 else rung, lmin)  # lmin 0: all receivers (each pair once in FP32)
             sr.forces(pos, precision, acc)
             sr.rung_kick(mom, acc, rung, state, lmin, k, dt, eta, eps, synchronize=last_of_period and s == sub)
             if long_range is not None and s == sub:

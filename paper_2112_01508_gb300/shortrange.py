@@ -46,7 +46,8 @@ class ShortRange:
     """Short-range P3M force context for ``n`` particles (see include/p3m_sr.h)."""
 
     def __init__(self, n: int, x_s: float, x_r: float, G_m: float, softening: str | int = "bspline",
-                 eps: float = 0.0, n_sub=2, n_rung: int = 8, box: float = 1.0, device=None, stream=None):
+                 eps: float = 0.0, n_sub=2, n_rung: int = 8, box: float = 1.0, device=None, stream=None,
+                 symmetric: bool = True):
         nat.load()
         dev = torch.device("cuda") if device is None else torch.device(device)
         if dev.type != "cuda":
@@ -68,6 +69,7 @@ class ShortRange:
         if st != nat.P3M_OK:
             raise nat.P3MError(st, "p3m_sr_create failed (check parameters / device memory)")
         self._ctx = ctx
+        self.set_symmetric(symmetric)
 
     @classmethod
     def from_workload(cls, w, **kw):
@@ -99,6 +101,12 @@ class ShortRange:
             raise nat.P3MError(st, nat.p3m_sr_last_error(self._ctx))
 
     # -- entry points ------------------------------------------------------------
+    def set_symmetric(self, enable: bool):
+        """All-active FP32 forces: evaluate each pair once and update both particles
+        (True, p3m_sr_set_symmetric) or gather per receiver, bitwise reproducible (False)."""
+        self._raise(nat.p3m_sr_set_symmetric(self._ctx, bool(enable)))
+        self.symmetric = bool(enable)
+
     def set_subtiles(self, n_sub):
         """Change the subtiles per tile (p3m_sr_set_subtiles); sort again before the next force call."""
         ns = (n_sub,) * 3 if isinstance(n_sub, int) else tuple(int(v) for v in n_sub)

@@ -14,7 +14,7 @@ def rel_rms(a, ref):
 
 
 def gpu_forces(pos, x_s, x_r, G_m, softening="bspline", eps=0.0, precision=32, rung=None, rung_min=0,
-               n_sub=2, n_rung=8, return_ctx=False):
+               n_sub=2, n_rung=8, return_ctx=False, symmetric=True, box=1.0):
     """Sort + build_pairs + forces on the GPU; accelerations returned in the input order.
 
     Inactive receivers' rows come back as NaN (the output is pre-filled with NaN
@@ -22,7 +22,8 @@ def gpu_forces(pos, x_s, x_r, G_m, softening="bspline", eps=0.0, precision=32, r
     n = pos.shape[1]
     dev = torch.device("cuda")
     p = torch.from_numpy(np.ascontiguousarray(pos)).to(dev)
-    sr = ShortRange(n, x_s, x_r, G_m, softening=softening, eps=eps, n_sub=n_sub, n_rung=n_rung)
+    sr = ShortRange(n, x_s, x_r, G_m, softening=softening, eps=eps, n_sub=n_sub, n_rung=n_rung,
+                    symmetric=symmetric, box=box)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     carry = []
     rg = None

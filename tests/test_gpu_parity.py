@@ -173,3 +173,44 @@ def test_tabulated_variant_error(n32k):
     print("tabulated rel RMS:", errs)
     assert errs[14] < errs[12] < errs[10]
     assert errs[12] < 0.1  # ~6.5% on this set (3.8% on the 128^3 set)
+
+
+def _small_box_set():
+    """Four tiles per side (x_r = 0.24): one receiver chunk spans a whole row of
+    tiles, so two particles of one chunk can interact through a periodic image."""
+    rng = np.random.default_rng(21)
+    pos = rng.random((3, 3000))
+    pos[2, :400] = rng.random(400) * 0.03            # near z = 0 ...
+    pos[2, 400:800] = 1.0 - rng.random(400) * 0.03   # ... and near z = 1, same rows
+    pos[:2, 400:800] = pos[:2, :400] + 1e-3 * rng.normal(size=(2, 400))
+    return np.mod(pos, 1.0)
+
+
+@pytest.mark.parametrize("case", ["n32k", "small_box", "ragged_dense"])
+def test_fp32_symmetric_matches_gather_and_oracle(n32k, case):
+    """All-active FP32: the Newton-III kernel (each pair once, both particles
+    updated; Section 2.1.3 tile pairing) and the gathering kernel (each pair from
+    both sides) both match the oracle, count the same pairs, and the symmetric
+    sums conserve momentum to FP32 rounding."""
+    if case == "n32k":
+        pos, refs = n32k
+        x_s, x_r, G_m, eps = W1.x_s, W1.x_r, W1.G_m, W1.eps
+        ref, pairs = refs["bspline"]
+    else:
+        if case == "small_box":
+            pos, x_r = _small_box_set(), 0.24
+        else:
+            rng = np.random.default_rng(5)
+            pos, x_r = 0.5 + 0.02 * rng.random((3, 4097)), 0.1
+        x_s, G_m, eps = x_r / 4.5, 1.0 / pos.shape[1], 0.004
+        ref, pairs = oracle.sr_accel(pos, x_s, x_r, G_m, "bspline", eps)
+    rs = gpu_forces(pos, x_s, x_r, G_m, "bspline", eps, precision=32, symmetric=True)
+    rg = gpu_forces(pos, x_s, x_r, G_m, "bspline", eps, precision=32, symmetric=False)
+    for r in (rs, rg):
+        assert np.isfinite(r["acc"]).all()
+        assert abs(r["pairs"] - pairs) <= max(2, 1e-6 * pairs)
+        assert rel_rms(r["acc"], ref) <= FP32_TOL
+    assert rel_rms(rs["acc"], rg["acc"]) <= 1e-6
+    # Newton's third law: the net force vanishes up to FP32 rounding of the sums
+    net = np.abs(rs["acc"].sum(axis=1)).max()
+    assert net <= 1e-6 * np.abs(rs["acc"]).sum(axis=1).max()
