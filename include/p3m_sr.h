@@ -207,8 +207,10 @@ p3m_status p3m_sr_forces(p3m_sr_ctx* ctx, const double* pos, int precision, void
  * roles); the per-particle sums are FP32 atomics into a context buffer.
  * enable = 0: every receiver gathers its own sum over all its partners, each
  * pair being evaluated from both sides; the result is then bitwise
- * reproducible.  Partially active sets, the FP64 path, the tabulated variant
- * and the vjp always gather.  P3M_ERR_INVALID for a NULL context.
+ * reproducible.  The FP32 vjp follows the same setting for any active set
+ * (its pair term is antisymmetric in the pair too, and every particle gets a
+ * gradient).  Partially active force calls, the FP64 path and the tabulated
+ * variant always gather.  P3M_ERR_INVALID for a NULL context.
  */
 p3m_status p3m_sr_set_symmetric(p3m_sr_ctx* ctx, int enable);
 
@@ -301,7 +303,10 @@ p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom, int mom_p
  *   xbar_k = sum_{j != k, r_kj < x_r} J_kj (abar_k [k active] - abar_j [j active]),
  *   J_kj = phi(r) I + (phi'(r)/r) x_kj x_kj^T,   phi = -G m B.
  * Active means receiver of the last p3m_sr_build_pairs.  Every particle gets a
- * gradient (suppliers move the receivers' accelerations too).
+ * gradient (suppliers move the receivers' accelerations too).  The pair term
+ * changes sign under k <-> j, so the FP32 path evaluates each pair once and
+ * adds the term to both with atomics (p3m_sr_set_symmetric; its last bits then
+ * depend on the order of execution).
  *   pos          3 x n float64 SoA device (sorted order)
  *   acc_bar      3 x n device, float (precision 32) or double (64)
  *   pos_bar_out  3 x n device, same type; every row is overwritten.

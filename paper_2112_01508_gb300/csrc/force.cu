@@ -877,6 +877,10 @@ struct SymSmem {
   float2 sz[kWarp];   // (-z_a, -z_b)
   int2 sj[kWarp];     // (j_a, j_b): sorted indices, -1 for padding
 };
+struct SymVjpSmem : SymSmem {
+  float4 vxy[kWarp];  // adjoint: the suppliers' masked abar, negated, in the layout of sxy / sz
+  float2 vz[kWarp];
+};
 
 #ifndef P3M_SYM_MINBLOCKS
 #define P3M_SYM_MINBLOCKS 4
@@ -893,16 +897,26 @@ __device__ __forceinline__ f2 shfl_xor2(f2 v, int o) {
   return r;
 }
 
-template <int SOFT>
+// VJP = true: the adjoint with the same traversal.  Its pair term J_ij (v_i - v_j),
+// v the masked abar, is antisymmetric in (i, j) like the force, so the partner
+// receives the negated term; every particle is a receiver.
+template <int SOFT, bool VJP = false>
 __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(TraversalArgs a, float4* __restrict__ acc4) {
-  __shared__ SymSmem smem[kPWarps];
+  using Smem = typename std::conditional<VJP, SymVjpSmem, SymSmem>::type;
+  __shared__ Smem smem[kPWarps];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  SymSmem& S = smem[threadIdx.x >> 5];
+  Smem& S = smem[threadIdx.x >> 5];
   float* sxy = (float*)S.sxy;
   float* szf = (float*)S.sz;
   int* sjf = (int*)S.sj;
+  float* vxy = nullptr;
+  float* vzf = nullptr;
+  if constexpr (VJP) {
+    vxy = (float*)S.vxy;
+    vzf = (float*)S.vz;
+  }
   const int n_chunks = *a.n_chunks;
   const Reach rc = make_reach(a);
   const float xr2 = a.f.xr2_f;
@@ -918,17 +932,29 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
     const int c_end = ch.start + ch.count;
     const float rx = F.valid ? F.pi.x : kSymPad, ry = F.valid ? F.pi.y : kSymPad, rz = F.valid ? F.pi.z : kSymPad;
     const f2 px = pk(rx, rx), py = pk(ry, ry), pz = pk(rz, rz);
+    f2 vix = pk(0.f, 0.f), viy = pk(0.f, 0.f), viz = pk(0.f, 0.f);  // adjoint: the receiver's masked abar
+    if constexpr (VJP) {
+      const float4 ab = F.valid ? a.abar4[F.pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+      vix = pk(ab.x, ab.x);
+      viy = pk(ab.y, ab.y);
+      viz = pk(ab.z, ab.z);
+    }
     f2 ax = pk(0.f, 0.f), ay = pk(0.f, 0.f), az = pk(0.f, 0.f);
     f2 hitsf = pk(0.f, 0.f);
     int cnt = 0;                          // staged suppliers (warp-uniform)
     bool blk_near = false, blk_own = false;  // the staged block holds a supplier near the box / of this chunk
 
-    auto stage = [&](int rank, const Vec3<float>& pj, int j) {
+    auto stage = [&](int rank, const Vec3<float>& pj, int j, const float4& aj) {
       const int q = rank & (kWarp - 1), h = rank >> 5;
       sxy[4 * q + h] = -pj.x;
       sxy[4 * q + 2 + h] = -pj.y;
       szf[2 * q + h] = -pj.z;
       sjf[2 * q + h] = j;
+      if constexpr (VJP) {
+        vxy[4 * q + h] = -aj.x;
+        vxy[4 * q + 2 + h] = -aj.y;
+        vzf[2 * q + h] = -aj.z;
+      }
     };
 
     // Evaluate the staged block of nsup suppliers (1 <= nsup <= 64) against the chunk.
@@ -945,12 +971,22 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
           sxy[4 * q + 3] = sxy[4 * lane + 2];
           szf[2 * q + 1] = szf[2 * lane];
           sjf[2 * q + 1] = sjf[2 * lane];
+          if constexpr (VJP) {
+            vxy[4 * q + 1] = vxy[4 * lane];
+            vxy[4 * q + 3] = vxy[4 * lane + 2];
+            vzf[2 * q + 1] = vzf[2 * lane];
+          }
         }
         if (lane < P && lane + P >= nsup) {
           sxy[4 * lane + 1] = kSymPad;
           sxy[4 * lane + 3] = kSymPad;
           szf[2 * lane + 1] = kSymPad;
           sjf[2 * lane + 1] = -1;
+          if constexpr (VJP) {
+            vxy[4 * lane + 1] = 0.f;
+            vxy[4 * lane + 3] = 0.f;
+            vzf[2 * lane + 1] = 0.f;
+          }
         }
         __syncwarp();
       }
@@ -967,44 +1003,103 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
           const f2 dx = add2(px, pk(s.x, s.y));
           const f2 dy = add2(py, pk(s.z, s.w));
           const f2 dz = add2(pz, pk(z.x, z.y));
-          const f2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, pk(kR2Floor, kR2Floor))));
-          float q0, q1;
-          upk(r2, q0, q1);
-          // No skip of steps without a hit: with 32 different pairs per step
-          // almost every step has one, and the vote costs more than it saves.
-          float c0 = fma_sat(q0, -kCutScale, xr2s), c1 = fma_sat(q1, -kCutScale, xr2s);
-          if (kMasked) {
-            const int2 jj = S.sj[q];
-            c0 = jj.x > i_self ? c0 : 0.f;
-            c1 = jj.y > i_self ? c1 : 0.f;
-          }
-          const f2 cm = pk(c0, c1);
-          hitsf = add2(hitsf, cm);
-          f2 B = bracket_main_f32x2<SOFT>(r2, a.f);
-          // softened branch: a cheap vote first, the exact condition (a hit,
-          // not a zero displacement) only when some pair is that close
-          if (kCheckSoft && __any_sync(full, fminf(q0, q1) < a.f.rsw2_f)) {
-            const bool rare0 = c0 > 0.f && q0 < a.f.rsw2_f && q0 > kR2Self;
-            const bool rare1 = c1 > 0.f && q1 < a.f.rsw2_f && q1 > kR2Self;
-            if (__any_sync(full, rare0 || rare1)) {
-              float b0, b1, Ds;
-              upk(B, b0, b1);
-#pragma unroll 1
-              for (int t = 0; t < 2; ++t) {  // one copy of the softened branch for both halves
-                const float sv = bracket_soft_f32<SOFT, false>(t ? q1 : q0, a.f, a.sc, Ds);
-                if (t == 0 && rare0) b0 = sv;
-                if (t == 1 && rare1) b1 = sv;
-              }
-              B = pk(b0, b1);
+          if constexpr (!VJP) {
+            const f2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, pk(kR2Floor, kR2Floor))));
+            float q0, q1;
+            upk(r2, q0, q1);
+            // No skip of steps without a hit: with 32 different pairs per step
+            // almost every step has one, and the vote costs more than it saves.
+            float c0 = fma_sat(q0, -kCutScale, xr2s), c1 = fma_sat(q1, -kCutScale, xr2s);
+            if (kMasked) {
+              const int2 jj = S.sj[q];
+              c0 = jj.x > i_self ? c0 : 0.f;
+              c1 = jj.y > i_self ? c1 : 0.f;
             }
+            const f2 cm = pk(c0, c1);
+            hitsf = add2(hitsf, cm);
+            f2 B = bracket_main_f32x2<SOFT>(r2, a.f);
+            // softened branch: a cheap vote first, the exact condition (a hit,
+            // not a zero displacement) only when some pair is that close
+            if (kCheckSoft && __any_sync(full, fminf(q0, q1) < a.f.rsw2_f)) {
+              const bool rare0 = c0 > 0.f && q0 < a.f.rsw2_f && q0 > kR2Self;
+              const bool rare1 = c1 > 0.f && q1 < a.f.rsw2_f && q1 > kR2Self;
+              if (__any_sync(full, rare0 || rare1)) {
+                float b0, b1, Ds;
+                upk(B, b0, b1);
+#pragma unroll 1
+                for (int t = 0; t < 2; ++t) {  // one copy of the softened branch for both halves
+                  const float sv = bracket_soft_f32<SOFT, false>(t ? q1 : q0, a.f, a.sc, Ds);
+                  if (t == 0 && rare0) b0 = sv;
+                  if (t == 1 && rare1) b1 = sv;
+                }
+                B = pk(b0, b1);
+              }
+            }
+            B = mul2(B, cm);
+            ax = fma2(B, dx, ax);
+            ay = fma2(B, dy, ay);
+            az = fma2(B, dz, az);
+            sax = fma2(B, dx, sax);
+            say = fma2(B, dy, say);
+            saz = fma2(B, dz, saz);
+          } else {
+            // adjoint: B and D = B'(r)/r, the term B v + D (x_ij . v) x_ij, v = abar_i - abar_j
+            // (no r^2 floor: a zero displacement is either masked, the receiver itself,
+            // or a coincident pair, which takes the softened branch)
+            const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+            float q0, q1;
+            upk(r2, q0, q1);
+            float c0 = fma_sat(q0, -kCutScale, xr2s), c1 = fma_sat(q1, -kCutScale, xr2s);
+            if (kMasked) {
+              const int2 jj = S.sj[q];
+              c0 = jj.x > i_self ? c0 : 0.f;
+              c1 = jj.y > i_self ? c1 : 0.f;
+            }
+            const f2 cm = pk(c0, c1);
+            hitsf = add2(hitsf, cm);
+            const float4 w = S.vxy[q];
+            const float2 wz = S.vz[q];
+            const f2 vx = add2(vix, pk(w.x, w.y));
+            const f2 vy = add2(viy, pk(w.z, w.w));
+            const f2 vz2 = add2(viz, pk(wz.x, wz.y));
+            f2 D;
+            f2 B = bracket_main_vjp_f32x2<SOFT>(r2, a.f, D);
+            if (kCheckSoft && __any_sync(full, fminf(q0, q1) < a.f.rsw2_f)) {
+              const bool rare0 = c0 > 0.f && q0 < a.f.rsw2_f;
+              const bool rare1 = c1 > 0.f && q1 < a.f.rsw2_f;
+              if (__any_sync(full, rare0 || rare1)) {
+                float b0, b1, d0, d1;
+                upk(B, b0, b1);
+                upk(D, d0, d1);
+#pragma unroll 1
+                for (int t = 0; t < 2; ++t) {
+                  float Ds;
+                  const float sv = bracket_soft_f32<SOFT, true>(t ? q1 : q0, a.f, a.sc, Ds);
+                  if (t == 0 && rare0) { b0 = sv; d0 = Ds; }
+                  if (t == 1 && rare1) { b1 = sv; d1 = Ds; }
+                }
+                B = pk(b0, b1);
+                D = pk(d0, d1);
+              }
+            }
+            if (kMasked) {  // selects: the receiver itself (r = 0) has non-finite main-branch values
+              float b0, b1, d0, d1;
+              upk(B, b0, b1);
+              upk(D, d0, d1);
+              B = pk(c0 > 0.f ? b0 : 0.f, c1 > 0.f ? b1 : 0.f);
+              D = pk(c0 > 0.f ? d0 : 0.f, c1 > 0.f ? d1 : 0.f);
+            } else {
+              B = mul2(B, cm);
+              D = mul2(D, cm);
+            }
+            const f2 cc = mul2(D, fma2(dx, vx, fma2(dy, vy, mul2(dz, vz2))));
+            ax = fma2(B, vx, fma2(cc, dx, ax));
+            ay = fma2(B, vy, fma2(cc, dy, ay));
+            az = fma2(B, vz2, fma2(cc, dz, az));
+            sax = fma2(B, vx, fma2(cc, dx, sax));
+            say = fma2(B, vy, fma2(cc, dy, say));
+            saz = fma2(B, vz2, fma2(cc, dz, saz));
           }
-          B = mul2(B, cm);
-          ax = fma2(B, dx, ax);
-          ay = fma2(B, dy, ay);
-          az = fma2(B, dz, az);
-          sax = fma2(B, dx, sax);
-          say = fma2(B, dy, say);
-          saz = fma2(B, dz, saz);
           // the pair of lane l + 1 comes to lane l, with its accumulator
           sax = shfl2(sax, src);
           say = shfl2(say, src);
@@ -1063,18 +1158,23 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
           unsigned dn;
           bool vn = locate(0, jn, dn);
           float4 rn = vn ? a.rel4[jn] : make_float4(0.f, 0.f, 0.f, 0.f);
+          float4 an = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (VJP && vn) an = a.abar4[jn];
           for (int b = 0;; b += kWarp) {
             const bool more = b < total;  // warp-uniform
             bool keep = false, near = false, own = false;
             Vec3<float> pj = {0.f, 0.f, 0.f};
             int j = 0, rank = 0, ns = 0;
+            float4 aj = make_float4(0.f, 0.f, 0.f, 0.f);
             if (more) {
               const bool have = vn;
               const float4 r = rn;
               const unsigned dpk = dn;
               j = jn;
+              if (VJP) aj = an;
               vn = (b + kWarp < total) ? locate(b + kWarp, jn, dn) : false;
               if (vn) rn = a.rel4[jn];
+              if (VJP && vn) an = a.abar4[jn];
               if (have) {
                 int ddx, ddy, ddz;
                 unpack_delta(dpk, ddx, ddy, ddz);
@@ -1092,7 +1192,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
               const unsigned m = __ballot_sync(full, keep);
               ns = __popc(m);
               rank = cnt + __popc(m & lt_mask);
-              if (keep && rank < 2 * kWarp) stage(rank, pj, j);
+              if (keep && rank < 2 * kWarp) stage(rank, pj, j, aj);
               blk_near = blk_near || __any_sync(full, near && rank < 2 * kWarp);
               blk_own = blk_own || __any_sync(full, own && rank < 2 * kWarp);
             }
@@ -1103,7 +1203,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
               if (more) {
                 blk_near = __any_sync(full, near && rank >= 2 * kWarp);
                 blk_own = __any_sync(full, own && rank >= 2 * kWarp);
-                if (keep && rank >= 2 * kWarp) stage(rank - 2 * kWarp, pj, j);
+                if (keep && rank >= 2 * kWarp) stage(rank - 2 * kWarp, pj, j, aj);
                 cnt += ns - 2 * kWarp;
               } else {
                 cnt = 0;
@@ -1131,7 +1231,8 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
   if (lane == 0 && pair_total) atomicAdd(a.pairs, pair_total);
 }
 
-// acc = -G m * (sum over partners of B(r) (x_i - x_j)), from the float4 sums of k_force_sym.
+// acc = -G m * (sum over partners of B(r) (x_i - x_j)) (or the adjoint's sum), from
+// the float4 sums of k_force_sym.
 __global__ void k_sym_finish(const float4* __restrict__ acc4, int64_t n, float scale, float* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float4 v = acc4[i];
@@ -1334,35 +1435,37 @@ static cudaError_t launch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
   return cudaGetLastError();
 }
 
-// Newton-III FP32 forward (all particles receivers): zero the float4 sums, run
-// k_force_sym, scale the sums into a.out.
-template <int SOFT>
+// Newton-III FP32 forward (all particles receivers) or adjoint: zero the float4
+// sums, run k_force_sym, scale the sums into a.out.
+template <int SOFT, bool VJP>
 static cudaError_t launch_sym_soft(p3m_sr_ctx* ctx, const TraversalArgs& a, float4* acc4) {
   static int blocks_per_sm = 0;
   if (blocks_per_sm == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_force_sym<SOFT>, kPThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_force_sym<SOFT, VJP>, kPThreads, 0);
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
   cudaStream_t s = ctx->stream;
   cudaError_t e = cudaMemsetAsync(acc4, 0, sizeof(float4) * (size_t)ctx->n, s);
   if (e != cudaSuccess) return e;
-  cudaEventRecord(ctx->kt_ev[0], s);
-  k_force_sym<SOFT><<<(unsigned)(ctx->num_sms * blocks_per_sm), kPThreads, 0, s>>>(a, acc4);
+  const int slot = VJP ? 1 : 0;
+  cudaEventRecord(ctx->kt_ev[2 * slot], s);
+  k_force_sym<SOFT, VJP><<<(unsigned)(ctx->num_sms * blocks_per_sm), kPThreads, 0, s>>>(a, acc4);
   ++ctx->launches;
-  cudaEventRecord(ctx->kt_ev[1], s);
-  ctx->kt_pending[0] = true;
+  cudaEventRecord(ctx->kt_ev[2 * slot + 1], s);
+  ctx->kt_pending[slot] = true;
   const unsigned fin = (unsigned)std::min<int64_t>((ctx->n + 255) / 256, (int64_t)ctx->num_sms * 16);
   k_sym_finish<<<fin, 256, 0, s>>>(acc4, ctx->n, -(float)a.f.G_m, (float*)a.out);
   ++ctx->launches;
   return cudaGetLastError();
 }
 
+template <bool VJP>
 static cudaError_t launch_sym(p3m_sr_ctx* ctx, const TraversalArgs& a) {
   float4* acc4 = (float4*)ctx->gather_tmp;  // 32 n bytes, idle outside the sort
   switch (ctx->prm.softening) {
-    case P3M_SOFT_NONE: return launch_sym_soft<P3M_SOFT_NONE>(ctx, a, acc4);
-    case P3M_SOFT_PLUMMER: return launch_sym_soft<P3M_SOFT_PLUMMER>(ctx, a, acc4);
-    default: return launch_sym_soft<P3M_SOFT_BSPLINE>(ctx, a, acc4);
+    case P3M_SOFT_NONE: return launch_sym_soft<P3M_SOFT_NONE, VJP>(ctx, a, acc4);
+    case P3M_SOFT_PLUMMER: return launch_sym_soft<P3M_SOFT_PLUMMER, VJP>(ctx, a, acc4);
+    default: return launch_sym_soft<P3M_SOFT_BSPLINE, VJP>(ctx, a, acc4);
   }
 }
 
@@ -1484,7 +1587,7 @@ extern "C" p3m_status p3m_sr_forces(p3m_sr_ctx* ctx, const double* pos, int prec
   a.active_idx = ctx->all_active ? nullptr : ctx->active_idx;
   a.out = acc_out;
   cudaError_t e;
-  if (precision == 32 && ctx->all_active && ctx->symmetric) e = launch_sym(ctx, a);
+  if (precision == 32 && ctx->all_active && ctx->symmetric) e = launch_sym<false>(ctx, a);
   else e = (precision == 32) ? dispatch_traverse<float, false>(ctx, a) : dispatch_traverse<double, false>(ctx, a);
   if ((st = cuda_check(ctx, e, "force kernel")) != P3M_OK) return st;
   report_latched(ctx);
@@ -1630,7 +1733,9 @@ extern "C" p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precisi
   a.out = pos_bar_out;
   a.abar4 = ctx->abar4;
   a.abar_d = ctx->abar_d;
-  cudaError_t e = (precision == 32) ? dispatch_traverse<float, true>(ctx, a) : dispatch_traverse<double, true>(ctx, a);
+  cudaError_t e;
+  if (precision == 32 && ctx->symmetric) e = launch_sym<true>(ctx, a);  // each pair once (any active set)
+  else e = (precision == 32) ? dispatch_traverse<float, true>(ctx, a) : dispatch_traverse<double, true>(ctx, a);
   if ((st = cuda_check(ctx, e, "vjp kernel")) != P3M_OK) return st;
   report_latched(ctx);
   return P3M_OK;
