@@ -53,7 +53,8 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 18, help="receivers in the CPU-oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1 << 14, help="receivers per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["forces32", "forces32_gather", "forces64", "vjp32", "sort", "pm32"],
+    ap.add_argument("--only", choices=["forces32", "forces32_gather", "forces64", "vjp32", "sort", "pm32",
+                                       "rung_steps"],
                     default=None,
                     help="profiling mode: run just one kernel family (no contract line)")
     return ap.parse_args()
@@ -594,7 +595,7 @@ def run_only(args):
     sr.build_pairs()
     acc32 = torch.zeros((3, w.n), dtype=torch.float32, device=dev)
     acc64 = torch.zeros((3, w.n), dtype=torch.float64, device=dev)
-    abar = torch.randn((3, w.n), dtype=torch.float32, device=dev)
+    abar = torch.randn((3, w.n), dtype=torch.float32, device=dev) if args.only == "vjp32" else None
     times = []
     if args.only == "pm32":
         from paper_2112_01508_gb300 import LongRange
@@ -606,6 +607,36 @@ def run_only(args):
                     times.append({"total": st.total_ms, "assign": st.assign_ms, "fft": st.fft_ms,
                                   "green": st.kernel_ms, "ifft": st.ifft_ms, "interp": st.interp_ms})
         print(json.dumps({"only": args.only, "workload": w.name, "mesh_ms": times, "n_phi": w.n_phi}))
+        sr.close()
+        return
+    if args.only == "rung_steps":
+        # the full step (all particles receivers) and the deepest-rung substep (~1% of the
+        # particles on rung 7 by the fake kick's |a|, Eq. rung), FP32 and FP64 paths
+        eta, n_rung = 0.025, 8
+        res = {"only": args.only, "workload": w.name, "n": w.n}
+        ts = []
+        for k in range(args.warmup + args.steps):
+            sr.forces(pos, 32, acc32)
+            if k >= args.warmup:
+                ts.append(sr.stats().force_kernel_ms)
+        st = sr.stats()
+        res["full_fp32"] = {"kernel_ms": ts, "pairs": st.pairs_last}
+        amag = torch.linalg.vector_norm(acc32, dim=0)
+        pick = torch.randperm(w.n, device=dev, generator=torch.Generator(device=dev).manual_seed(0))[:1 << 20]
+        q99 = float(torch.quantile(amag[pick], 0.99))
+        del amag, pick
+        dt = 64.0 * (2.0 * eta * w.eps / q99) ** 0.5
+        rung = sr.assign_rungs(acc32, dt, eta, w.eps)
+        sr.build_pairs(rung, n_rung - 1)
+        for prec, out in ((32, acc32), (64, acc64)):
+            ts = []
+            for k in range(args.warmup + args.steps if prec == 32 else 1):
+                sr.forces(pos, prec, out)
+                if prec == 64 or k >= args.warmup:
+                    ts.append(sr.stats().force_kernel_ms)
+            st = sr.stats()
+            res[f"deepest_rung_fp{prec}"] = {"kernel_ms": ts, "pairs": st.pairs_last, "receivers": st.n_active}
+        print(json.dumps(res))
         sr.close()
         return
     if args.only == "forces32_gather":
