@@ -876,12 +876,15 @@ struct SymSmem {
   float4 sxy[kWarp];  // pair q: (-x_a, -x_b, -y_a, -y_b) of suppliers a = q and b = q + P
   float2 sz[kWarp];   // (-z_a, -z_b)
   int2 sj[kWarp];     // (j_a, j_b): sorted indices, -1 for padding
+  int rq[3 * kWarp];  // forward: pairs closer than r_sw (receiver lane | pair << 5 | half << 10)
 };
 struct SymVjpSmem : SymSmem {
   float4 vxy[kWarp];  // adjoint: the suppliers' masked abar, negated, in the layout of sxy / sz
   float2 vz[kWarp];
 };
 
+// 4 resident blocks of 4 warps per SM leave the kernel 128 registers; measured
+// best on the 128^3 set against 5 and 6 blocks (which spill).
 #ifndef P3M_SYM_MINBLOCKS
 #define P3M_SYM_MINBLOCKS 4
 #endif
@@ -994,6 +997,26 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
       const int src = (lane & ~qmask) | ((lane + 1) & qmask);
       f2 sax = pk(0.f, 0.f), say = pk(0.f, 0.f), saz = pk(0.f, 0.f);
       int q = lane & qmask;
+      int nq = 0;  // forward: queued close pairs (warp-uniform)
+      // Evaluate queued close pairs [base, base + count) (count <= 32), one per lane,
+      // with the softened form, and add them to both particles.
+      auto run_rare = [&](int base, int count) {
+        const int e = lane < count ? S.rq[base + lane] : 0;
+        const int rl = e & (kWarp - 1);
+        const float xr = __shfl_sync(full, rx, rl), yr = __shfl_sync(full, ry, rl), zr = __shfl_sync(full, rz, rl);
+        const int ir = __shfl_sync(full, i_self, rl);
+        if (lane < count) {
+          const int qe = (e >> 5) & (kWarp - 1), he = e >> 10;
+          const float ex = xr + sxy[4 * qe + he], ey = yr + sxy[4 * qe + 2 + he], ez = zr + szf[2 * qe + he];
+          const float r2s = fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, kR2Floor)));
+          float Ds;
+          const float Bs = bracket_soft_f32<SOFT, false>(r2s, a.f, a.sc, Ds);
+          const int js = sjf[2 * qe + he];
+          atomicAdd(acc4 + ir, make_float4(Bs * ex, Bs * ey, Bs * ez, 0.f));
+          atomicAdd(acc4 + js, make_float4(-Bs * ex, -Bs * ey, -Bs * ez, 0.f));
+        }
+        __syncwarp();
+      };
       auto run = [&](auto check_soft, auto masked) {
         constexpr bool kCheckSoft = decltype(check_soft)::value;
         constexpr bool kMasked = decltype(masked)::value;
@@ -1018,21 +1041,28 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
             const f2 cm = pk(c0, c1);
             hitsf = add2(hitsf, cm);
             f2 B = bracket_main_f32x2<SOFT>(r2, a.f);
-            // softened branch: a cheap vote first, the exact condition (a hit,
-            // not a zero displacement) only when some pair is that close
+            // Pairs closer than r_sw (the softened form): a cheap vote first, the
+            // exact condition (a hit, not a zero displacement) only when some pair
+            // is that close.  Such pairs leave the step's sums and go to a queue
+            // that is evaluated 32 at a time, one per lane, so that the long
+            // softened branch runs with full warps.
             if (kCheckSoft && __any_sync(full, fminf(q0, q1) < a.f.rsw2_f)) {
               const bool rare0 = c0 > 0.f && q0 < a.f.rsw2_f && q0 > kR2Self;
               const bool rare1 = c1 > 0.f && q1 < a.f.rsw2_f && q1 > kR2Self;
-              if (__any_sync(full, rare0 || rare1)) {
-                float b0, b1, Ds;
+              const unsigned rb0 = __ballot_sync(full, rare0), rb1 = __ballot_sync(full, rare1);
+              if (rb0 | rb1) {
+                const int n0 = __popc(rb0);
+                if (rare0) S.rq[nq + __popc(rb0 & lt_mask)] = lane | (q << 5);
+                if (rare1) S.rq[nq + n0 + __popc(rb1 & lt_mask)] = lane | (q << 5) | 1024;
+                nq += n0 + __popc(rb1);
+                float b0, b1;
                 upk(B, b0, b1);
-#pragma unroll 1
-                for (int t = 0; t < 2; ++t) {  // one copy of the softened branch for both halves
-                  const float sv = bracket_soft_f32<SOFT, false>(t ? q1 : q0, a.f, a.sc, Ds);
-                  if (t == 0 && rare0) b0 = sv;
-                  if (t == 1 && rare1) b1 = sv;
+                B = pk(rare0 ? 0.f : b0, rare1 ? 0.f : b1);
+                __syncwarp();
+                while (nq >= kWarp) {
+                  nq -= kWarp;
+                  run_rare(nq, kWarp);
                 }
-                B = pk(b0, b1);
               }
             }
             B = mul2(B, cm);
@@ -1113,6 +1143,12 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
       } else {
         if (blk_own) run(std::false_type{}, std::true_type{});
         else run(std::false_type{}, std::false_type{});
+      }
+      if constexpr (!VJP) {
+        if (nq > 0) {  // the rest of the block's queue, while its suppliers are staged
+          run_rare(0, nq);
+          nq = 0;
+        }
       }
       // after P steps lane l holds the sum of its group for pair l mod P
       for (int o = P; o < kWarp; o <<= 1) {
