@@ -936,8 +936,9 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
     const float rx = F.valid ? F.pi.x : kSymPad, ry = F.valid ? F.pi.y : kSymPad, rz = F.valid ? F.pi.z : kSymPad;
     const f2 px = pk(rx, rx), py = pk(ry, ry), pz = pk(rz, rz);
     f2 vix = pk(0.f, 0.f), viy = pk(0.f, 0.f), viz = pk(0.f, 0.f);  // adjoint: the receiver's masked abar
+    float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
     if constexpr (VJP) {
-      const float4 ab = F.valid ? a.abar4[F.pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (F.valid) ab = a.abar4[F.pidx];
       vix = pk(ab.x, ab.x);
       viy = pk(ab.y, ab.y);
       viz = pk(ab.z, ab.z);
@@ -997,23 +998,44 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
       const int src = (lane & ~qmask) | ((lane + 1) & qmask);
       f2 sax = pk(0.f, 0.f), say = pk(0.f, 0.f), saz = pk(0.f, 0.f);
       int q = lane & qmask;
-      int nq = 0;  // forward: queued close pairs (warp-uniform)
+      int nq = 0;  // queued close pairs (warp-uniform)
       // Evaluate queued close pairs [base, base + count) (count <= 32), one per lane,
-      // with the softened form, and add them to both particles.
+      // with the softened form, and add their terms to both particles.
       auto run_rare = [&](int base, int count) {
         const int e = lane < count ? S.rq[base + lane] : 0;
         const int rl = e & (kWarp - 1);
         const float xr = __shfl_sync(full, rx, rl), yr = __shfl_sync(full, ry, rl), zr = __shfl_sync(full, rz, rl);
         const int ir = __shfl_sync(full, i_self, rl);
+        float vxr = 0.f, vyr = 0.f, vzr = 0.f;
+        if constexpr (VJP) {
+          vxr = __shfl_sync(full, ab.x, rl);
+          vyr = __shfl_sync(full, ab.y, rl);
+          vzr = __shfl_sync(full, ab.z, rl);
+        }
         if (lane < count) {
           const int qe = (e >> 5) & (kWarp - 1), he = e >> 10;
           const float ex = xr + sxy[4 * qe + he], ey = yr + sxy[4 * qe + 2 + he], ez = zr + szf[2 * qe + he];
-          const float r2s = fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, kR2Floor)));
-          float Ds;
-          const float Bs = bracket_soft_f32<SOFT, false>(r2s, a.f, a.sc, Ds);
           const int js = sjf[2 * qe + he];
-          atomicAdd(acc4 + ir, make_float4(Bs * ex, Bs * ey, Bs * ez, 0.f));
-          atomicAdd(acc4 + js, make_float4(-Bs * ex, -Bs * ey, -Bs * ez, 0.f));
+          float tx, ty, tz;
+          if constexpr (!VJP) {
+            const float r2s = fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, kR2Floor)));
+            float Ds;
+            const float Bs = bracket_soft_f32<SOFT, false>(r2s, a.f, a.sc, Ds);
+            tx = Bs * ex;
+            ty = Bs * ey;
+            tz = Bs * ez;
+          } else {  // B v + D (x_ij . v) x_ij with v = abar_i - abar_j
+            const float r2s = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            float Ds;
+            const float Bs = bracket_soft_f32<SOFT, true>(r2s, a.f, a.sc, Ds);
+            const float wx = vxr + vxy[4 * qe + he], wy = vyr + vxy[4 * qe + 2 + he], wz = vzr + vzf[2 * qe + he];
+            const float cd = Ds * fmaf(ex, wx, fmaf(ey, wy, ez * wz));
+            tx = fmaf(Bs, wx, cd * ex);
+            ty = fmaf(Bs, wy, cd * ey);
+            tz = fmaf(Bs, wz, cd * ez);
+          }
+          atomicAdd(acc4 + ir, make_float4(tx, ty, tz, 0.f));
+          atomicAdd(acc4 + js, make_float4(-tx, -ty, -tz, 0.f));
         }
         __syncwarp();
       };
@@ -1094,22 +1116,27 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
             const f2 vz2 = add2(viz, pk(wz.x, wz.y));
             f2 D;
             f2 B = bracket_main_vjp_f32x2<SOFT>(r2, a.f, D);
+            // close pairs (r < r_sw, coincident ones included) to the queue, as in
+            // the forward; selects, since the main branch is not finite at r = 0
             if (kCheckSoft && __any_sync(full, fminf(q0, q1) < a.f.rsw2_f)) {
               const bool rare0 = c0 > 0.f && q0 < a.f.rsw2_f;
               const bool rare1 = c1 > 0.f && q1 < a.f.rsw2_f;
-              if (__any_sync(full, rare0 || rare1)) {
+              const unsigned rb0 = __ballot_sync(full, rare0), rb1 = __ballot_sync(full, rare1);
+              if (rb0 | rb1) {
+                const int n0 = __popc(rb0);
+                if (rare0) S.rq[nq + __popc(rb0 & lt_mask)] = lane | (q << 5);
+                if (rare1) S.rq[nq + n0 + __popc(rb1 & lt_mask)] = lane | (q << 5) | 1024;
+                nq += n0 + __popc(rb1);
                 float b0, b1, d0, d1;
                 upk(B, b0, b1);
                 upk(D, d0, d1);
-#pragma unroll 1
-                for (int t = 0; t < 2; ++t) {
-                  float Ds;
-                  const float sv = bracket_soft_f32<SOFT, true>(t ? q1 : q0, a.f, a.sc, Ds);
-                  if (t == 0 && rare0) { b0 = sv; d0 = Ds; }
-                  if (t == 1 && rare1) { b1 = sv; d1 = Ds; }
+                B = pk(rare0 ? 0.f : b0, rare1 ? 0.f : b1);
+                D = pk(rare0 ? 0.f : d0, rare1 ? 0.f : d1);
+                __syncwarp();
+                while (nq >= kWarp) {
+                  nq -= kWarp;
+                  run_rare(nq, kWarp);
                 }
-                B = pk(b0, b1);
-                D = pk(d0, d1);
               }
             }
             if (kMasked) {  // selects: the receiver itself (r = 0) has non-finite main-branch values
@@ -1144,11 +1171,9 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
         if (blk_own) run(std::false_type{}, std::true_type{});
         else run(std::false_type{}, std::false_type{});
       }
-      if constexpr (!VJP) {
-        if (nq > 0) {  // the rest of the block's queue, while its suppliers are staged
-          run_rare(0, nq);
-          nq = 0;
-        }
+      if (nq > 0) {  // the rest of the block's queue, while its suppliers are staged
+        run_rare(0, nq);
+        nq = 0;
       }
       // after P steps lane l holds the sum of its group for pair l mod P
       for (int o = P; o < kWarp; o <<= 1) {
