@@ -188,3 +188,25 @@ def test_vjp_each_pair_once_matches_one_sided(rung_min):
     # two FP32 sums in different orders, each ~1e-6 from the FP64 oracle on this set
     # (the adjoint's v_i - v_j and D terms cancel more than the force's terms)
     assert rel_rms(got[True], got[False]) <= 5e-6
+
+
+@pytest.mark.parametrize("softening", ["plummer", "bspline"])
+def test_vjp_dense_cluster_with_coincident_particles(softening):
+    """FP32 adjoint on a dense cluster in which most pairs are closer than r_sw (the
+    close-pair queue overflows within a step) and 40 particles sit exactly on others
+    (r = 0: the softened B(0) acts on abar_i - abar_j), against the oracle."""
+    rng = np.random.default_rng(23)
+    x_r, eps = 0.1, 0.004
+    dense = 0.4 + 2e-3 * rng.normal(size=(3, 1500))
+    pos = np.concatenate([dense, rng.random((3, 1000)), dense[:, :40]], axis=1) % 1.0
+    n = pos.shape[1]
+    abar = rng.normal(size=(3, n))
+    ref = oracle.sr_vjp(pos, abar, x_r / 4.5, x_r, 1.0 / n, softening, eps)
+    with ShortRange(n, x_r / 4.5, x_r, 1.0 / n, softening=softening, eps=eps) as sr:
+        p = torch.from_numpy(pos.copy()).cuda()
+        sr.sort(p)
+        sr.build_pairs()
+        ab = sr.permute(torch.from_numpy(abar).cuda().float().contiguous())
+        xb = sr.unpermute(sr.vjp(p, ab, 32)).double().cpu().numpy()
+    assert np.isfinite(xb).all()
+    assert rel_rms(xb, ref) <= 1e-5, rel_rms(xb, ref)
