@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <type_traits>
+
 #include "ctx.cuh"
 
 namespace p3m {
@@ -13,10 +15,34 @@ namespace p3m {
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <class A>
-__global__ void k_rungs(const A* __restrict__ acc, int64_t n, double qq, int n_rung, int8_t* __restrict__ rung,
-                        int* __restrict__ err) {
+__global__ void k_rungs(const A* __restrict__ acc, int64_t n, double qq, float qqf, int n_rung,
+                        int8_t* __restrict__ rung, int* __restrict__ err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if constexpr (std::is_same<A, float>::value) {
+    // FP32 first: with FP32 accelerations (exact in FP64) and qqf = fl32(qq) the FP32
+    // s has a relative error below 7 x 2^-24.  The rung changes only where s crosses a
+    // power of 16; unless the FP32 s lies within 64 ulps of one, the FP64 s of the
+    // rule below is on the same side of every boundary and gives the same rung.
+    // Near a boundary, or out of the FP32 normal range, the FP64 path decides.
+    if (qqf > 0.0f) {  // 0: qq outside the FP32 normal range
+      const float fx = acc[i], fy = acc[n + i], fz = acc[2 * n + i];
+      const float a2f = __fadd_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)), __fmul_rn(fz, fz));
+      const float sf = __fmul_rn(qqf, a2f);
+      if (a2f >= 1e-30f && sf <= 1e30f) {  // false for NaN and infinity too
+        const int b = __float_as_int(sf);
+        const int e = ((b >> 23) & 0xff) - 127;
+        const int m = b & 0x7fffff;
+        const bool near = ((e & 3) == 0 && m < 64) || ((e & 3) == 3 && m > 0x7fffff - 64);
+        if (!near) {
+          int l = 0;
+          if (sf > 1.0f) l = min((e + (m != 0 ? 1 : 0) + 3) >> 2, n_rung - 1);
+          rung[i] = (int8_t)l;
+          return;
+        }
+      }
+    }
+  }
   double ax = (double)acc[i], ay = (double)acc[n + i], az = (double)acc[2 * n + i];
   // s = q^2 (|a|^2) with |a|^2 = (ax*ax + ay*ay) + az*az, each op correctly rounded
   double a2 = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
@@ -171,13 +197,16 @@ extern "C" p3m_status p3m_sr_assign_rungs(p3m_sr_ctx* ctx, const void* acc, int 
   volatile double t3 = t2 * eps;
   volatile double q = t1 / t3;
   double qq = q * q;
+  const float qqf = (qq >= 1e-30 && qq <= 1e30) ? (float)qq : 0.0f;  // FP32 first pass of k_rungs
   const int t = 256;
   if (acc_precision == 64)
-    { k_rungs<double><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>((const double*)acc, ctx->n, qq, ctx->prm.n_rung,
-                                                                   rung_out, ctx->err_dev); ++ctx->launches; }
+    { k_rungs<double><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>((const double*)acc, ctx->n, qq, qqf,
+                                                                   ctx->prm.n_rung, rung_out, ctx->err_dev);
+      ++ctx->launches; }
   else
-    { k_rungs<float><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>((const float*)acc, ctx->n, qq, ctx->prm.n_rung,
-                                                                  rung_out, ctx->err_dev); ++ctx->launches; }
+    { k_rungs<float><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>((const float*)acc, ctx->n, qq, qqf,
+                                                                  ctx->prm.n_rung, rung_out, ctx->err_dev);
+      ++ctx->launches; }
   if ((st = cuda_check(ctx, cudaGetLastError(), "rung kernel")) != P3M_OK) return st;
   report_latched(ctx);
   return P3M_OK;
