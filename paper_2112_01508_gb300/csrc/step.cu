@@ -14,39 +14,35 @@ namespace p3m {
 
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Eq. rung for the acceleration (ax, ay, az): the smallest l >= 0 with
+// s = qq |a|^2 <= 16^l, s = qq ((ax^2 + ay^2) + az^2) with each FP64 operation
+// correctly rounded, clamped to n_rung - 1; a non-finite s latches
+// kErrNonfiniteAcc and gives 0.
+//
+// FP32 accelerations take an FP32 first pass: they are exact in FP64, and with
+// qqf = fl32(qq) the FP32 s has a relative error below 7 x 2^-24.  The rung changes
+// only where s crosses a power of 16; unless the FP32 s lies within 64 ulps of one,
+// the FP64 s is on the same side of every boundary and gives the same rung.  Near
+// a boundary, or out of the FP32 normal range (qqf = 0 when qq is), the FP64 rule
+// decides.
 template <class A>
-__global__ void k_rungs(const A* __restrict__ acc, int64_t n, double qq, float qqf, int n_rung,
-                        int8_t* __restrict__ rung, int* __restrict__ err) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ int rung_rule(A ax, A ay, A az, double qq, float qqf, int n_rung, int* err) {
   if constexpr (std::is_same<A, float>::value) {
-    // FP32 first: with FP32 accelerations (exact in FP64) and qqf = fl32(qq) the FP32
-    // s has a relative error below 7 x 2^-24.  The rung changes only where s crosses a
-    // power of 16; unless the FP32 s lies within 64 ulps of one, the FP64 s of the
-    // rule below is on the same side of every boundary and gives the same rung.
-    // Near a boundary, or out of the FP32 normal range, the FP64 path decides.
-    if (qqf > 0.0f) {  // 0: qq outside the FP32 normal range
-      const float fx = acc[i], fy = acc[n + i], fz = acc[2 * n + i];
-      const float a2f = __fadd_rn(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)), __fmul_rn(fz, fz));
+    if (qqf > 0.0f) {
+      const float a2f = __fadd_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)), __fmul_rn(az, az));
       const float sf = __fmul_rn(qqf, a2f);
       if (a2f >= 1e-30f && sf <= 1e30f) {  // false for NaN and infinity too
         const int b = __float_as_int(sf);
         const int e = ((b >> 23) & 0xff) - 127;
         const int m = b & 0x7fffff;
         const bool near = ((e & 3) == 0 && m < 64) || ((e & 3) == 3 && m > 0x7fffff - 64);
-        if (!near) {
-          int l = 0;
-          if (sf > 1.0f) l = min((e + (m != 0 ? 1 : 0) + 3) >> 2, n_rung - 1);
-          rung[i] = (int8_t)l;
-          return;
-        }
+        if (!near) return sf > 1.0f ? min((e + (m != 0 ? 1 : 0) + 3) >> 2, n_rung - 1) : 0;
       }
     }
   }
-  double ax = (double)acc[i], ay = (double)acc[n + i], az = (double)acc[2 * n + i];
-  // s = q^2 (|a|^2) with |a|^2 = (ax*ax + ay*ay) + az*az, each op correctly rounded
-  double a2 = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
-  double s = __dmul_rn(qq, a2);
+  const double x = (double)ax, y = (double)ay, z = (double)az;
+  const double a2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+  const double s = __dmul_rn(qq, a2);
   int l = 0;
   if (isnan(s) || isinf(s)) {
     atomicOr(err, kErrNonfiniteAcc);
@@ -59,7 +55,18 @@ __global__ void k_rungs(const A* __restrict__ acc, int64_t n, double qq, float q
     l = (k + 3) >> 2;
     if (l > n_rung - 1) l = n_rung - 1;
   }
-  rung[i] = (int8_t)l;
+  return l;
+}
+
+// qqf: fl32(qq) for the FP32 first pass of rung_rule, or 0 to skip it.
+__host__ inline float rung_qqf(double qq) { return (qq >= 1e-30 && qq <= 1e30) ? (float)qq : 0.0f; }
+
+template <class A>
+__global__ void k_rungs(const A* __restrict__ acc, int64_t n, double qq, float qqf, int n_rung,
+                        int8_t* __restrict__ rung, int* __restrict__ err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  rung[i] = (int8_t)rung_rule<A>(acc[i], acc[n + i], acc[2 * n + i], qq, qqf, n_rung, err);
 }
 
 struct KickFactors {
@@ -129,7 +136,7 @@ __global__ void __launch_bounds__(256) k_drift(double* __restrict__ pos, const M
 template <class M, class A>
 __global__ void k_rung_kick(M* __restrict__ mom, const A* __restrict__ acc, int8_t* __restrict__ rung,
                             int8_t* __restrict__ state, int64_t n, int rung_min, long long k, int log2_sub, double dt,
-                            double qq, int n_rung, int sync, int* __restrict__ err) {
+                            double qq, float qqf, int n_rung, int sync, int* __restrict__ err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int l = rung[i];
@@ -142,29 +149,18 @@ __global__ void k_rung_kick(M* __restrict__ mom, const A* __restrict__ acc, int8
   const double f = st == 0 ? 1.0 : (st == 1 ? 0.5 : 0.75);
   const double fac = sync ? f - 0.5 : f;
   const double K = ldexp(__dmul_rn(dt, fac), -l);  // fac dt / 2^l (the scaling is exact)
-  double a[3];
+  A av[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    a[d] = (double)acc[d * n + i];
-    mom[d * n + i] = (M)__dadd_rn((double)mom[d * n + i], __dmul_rn(a[d], K));
+    av[d] = acc[d * n + i];
+    mom[d * n + i] = (M)__dadd_rn((double)mom[d * n + i], __dmul_rn((double)av[d], K));
   }
   if (sync) {
     state[i] = 0;
     return;
   }
-  // Eq. rung on the acceleration of this kick (same rule as k_rungs)
-  const double a2 = __dadd_rn(__dadd_rn(__dmul_rn(a[0], a[0]), __dmul_rn(a[1], a[1])), __dmul_rn(a[2], a[2]));
-  const double s = __dmul_rn(qq, a2);
-  int lnew = 0;
-  if (isnan(s) || isinf(s)) {
-    atomicOr(err, kErrNonfiniteAcc);
-  } else if (s > 1.0) {
-    long long b = __double_as_longlong(s);
-    int e = (int)((b >> 52) & 0x7ff) - 1023;
-    int kk = e + (((b & 0xfffffffffffffLL) != 0) ? 1 : 0);
-    lnew = (kk + 3) >> 2;
-    if (lnew > n_rung - 1) lnew = n_rung - 1;
-  }
+  // Eq. rung on the acceleration of this kick (the rule of k_rungs)
+  const int lnew = rung_rule<A>(av[0], av[1], av[2], qq, qqf, n_rung, err);
   int out = l, ost = 0;
   if (lnew > l) {
     out = l + 1;  // next kick: half of the finer rung's usual kick
@@ -197,7 +193,7 @@ extern "C" p3m_status p3m_sr_assign_rungs(p3m_sr_ctx* ctx, const void* acc, int 
   volatile double t3 = t2 * eps;
   volatile double q = t1 / t3;
   double qq = q * q;
-  const float qqf = (qq >= 1e-30 && qq <= 1e30) ? (float)qq : 0.0f;  // FP32 first pass of k_rungs
+  const float qqf = rung_qqf(qq);
   const int t = 256;
   if (acc_precision == 64)
     { k_rungs<double><<<blocks_for(ctx->n, t), t, 0, ctx->stream>>>((const double*)acc, ctx->n, qq, qqf,
@@ -304,16 +300,16 @@ extern "C" p3m_status p3m_sr_rung_kick(p3m_sr_ctx* ctx, void* mom, int mom_preci
   const int sy = synchronize ? 1 : 0;
   if (mom_precision == 64 && acc_precision == 32)
     k_rung_kick<double, float><<<b, t, 0, s>>>((double*)mom, (const float*)acc, rung, kick_state, n, rung_min, substep,
-                                               log2_sub, dt, qq, nr, sy, ctx->err_dev);
+                                               log2_sub, dt, qq, rung_qqf(qq), nr, sy, ctx->err_dev);
   else if (mom_precision == 64 && acc_precision == 64)
     k_rung_kick<double, double><<<b, t, 0, s>>>((double*)mom, (const double*)acc, rung, kick_state, n, rung_min,
-                                                substep, log2_sub, dt, qq, nr, sy, ctx->err_dev);
+                                                substep, log2_sub, dt, qq, rung_qqf(qq), nr, sy, ctx->err_dev);
   else if (mom_precision == 32 && acc_precision == 32)
     k_rung_kick<float, float><<<b, t, 0, s>>>((float*)mom, (const float*)acc, rung, kick_state, n, rung_min, substep,
-                                              log2_sub, dt, qq, nr, sy, ctx->err_dev);
+                                              log2_sub, dt, qq, rung_qqf(qq), nr, sy, ctx->err_dev);
   else
     k_rung_kick<float, double><<<b, t, 0, s>>>((float*)mom, (const double*)acc, rung, kick_state, n, rung_min,
-                                               substep, log2_sub, dt, qq, nr, sy, ctx->err_dev);
+                                               substep, log2_sub, dt, qq, rung_qqf(qq), nr, sy, ctx->err_dev);
   ++ctx->launches;
   if ((st = cuda_check(ctx, cudaGetLastError(), "rung kick kernel")) != P3M_OK) return st;
   report_latched(ctx);
