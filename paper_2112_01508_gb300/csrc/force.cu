@@ -22,9 +22,11 @@
 //      into the chunk frame by the integer subtile offset) and tests it against
 //      the bounding box; the survivors are broadcast to all lanes, and every
 //      lane evaluates its own (i, j) pair.
-// The FP32 forward kernel stages the survivors in shared memory as packed
-// pairs and evaluates two suppliers per step in f32x2 arithmetic; the FP64
-// forward and the adjoint broadcast survivors with warp shuffles.  Chunks are
+// The one-sided FP32 forward kernel stages the survivors in shared memory as
+// packed pairs and evaluates two suppliers per step in f32x2 arithmetic; the
+// FP64 forward and the one-sided adjoint broadcast survivors with warp
+// shuffles.  With every particle a receiver, the FP32 forward and the FP32
+// adjoint evaluate each pair once instead (k_force_sym, below).  Chunks are
 // handed out through an atomic counter to persistent warps, which balances the
 // strongly varying cost of clustered regions.
 #include <algorithm>
@@ -866,7 +868,9 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
 // lane to lane by warp shuffles; at the end of the block the groups' partial
 // sums are reduced and added, like the receivers' own sums at the end of the
 // chunk, into an FP32 float4 array with vector atomics.  k_sym_finish scales
-// that array into the caller's 3 x n output.
+// that array into the caller's 3 x n output.  Pairs closer than r_sw (the
+// softened form) leave the step's sums: they are queued per warp and evaluated
+// 32 at a time, one per lane, their terms added to both particles directly.
 // ---------------------------------------------------------------------------
 
 constexpr float kSymPad = 1e10f;  // padding supplier at -1e10, invalid receiver at +1e10: finite B, no hit
