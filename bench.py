@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 18, help="receivers in the CPU-oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1 << 14, help="receivers per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 512^3 and 1024^3 sub-records (full step, rung substeps, FP32 vs FP64)")
     ap.add_argument("--only", choices=["forces32", "forces32_gather", "forces64", "vjp32", "sort", "pm32",
                                        "rung_steps"],
                     default=None,
@@ -66,6 +68,21 @@ def source_hash(paths):
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+HBM_FALLBACK_GBS = 6800.0  # the profiling recipe's fallback, used only without MEASURED_PEAKS.json
+SORT_BYTES_PER_PARTICLE = 110  # read/write x, ids, perm, carried momenta and rungs (algorithmic)
+KICK_DRIFT_BYTES_PER_PARTICLE = 109  # read a (FP32) 12, r/w q 48, r/w x 48, write rung 1
+
+
+def hbm_peak():
+    """Measured copy bandwidth of this GPU (GB/s) and where it came from."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
 
 
 FORCE_SOURCES = ["paper_2112_01508_gb300/csrc/force.cu", "paper_2112_01508_gb300/csrc/pair_math.cuh",
@@ -192,6 +209,124 @@ def traffic_from_profiles(workload: str):
         return None
 
 
+def large_record(wname: str, dev, with_cpu: bool, steps: int = 2):
+    """Sub-record for a large workload (512^3: 8 rungs, per-rung substeps; 1024^3: full
+    step and deepest-rung substep, FP32 vs FP64).  The CPU-baseline leg runs the oracle
+    on 2^18 seeded receivers of the same state (all suppliers); the GPU outputs on those
+    receivers are compared with it."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2112_01508_gb300 import ShortRange
+
+    w = synth.workload(wname)
+    n = w.n
+    eta, n_rung = 0.025, 8
+    t0 = time.perf_counter()
+    pos_np = synth.workload_positions(w)
+    rec = {"workload": f"{w.name}: {w.description}", "n": n, "n_sub": w.n_sub, "softening": "bspline",
+           "generate_s": time.perf_counter() - t0}
+    stream = torch.cuda.current_stream(dev)
+    gen = torch.Generator(device=dev)
+    with ShortRange.from_workload(w, device=dev) as sr:
+        p = torch.from_numpy(pos_np).to(dev)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        sr.sort(p, perm_out=perm)
+        sr.build_pairs()
+        a32 = sr.forces(p, 32)
+        ts = []
+        for _ in range(2):
+            sr.forces(p, 32, a32)
+            ts.append(sr.stats().force_kernel_ms)
+        st = sr.stats()
+        peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / OPS_PER_PAIR
+        rec["full_fp32"] = {"pairs": st.pairs_last, "kernel_ms": statistics.mean(ts),
+                            "value": st.pairs_last / (statistics.mean(ts) * 1e-3), "unit": UNIT,
+                            "kernel": "k_force_sym<bspline> (each pair once)",
+                            "frac": st.pairs_last / (statistics.mean(ts) * 1e-3) / peak}
+        # rungs from the fake kick (Eq. rung), dt putting ~1% of the particles on rung 7
+        amag = torch.linalg.vector_norm(a32, dim=0)
+        gen.manual_seed(0)
+        q99 = float(torch.quantile(amag[torch.randperm(n, device=dev, generator=gen)[:1 << 20]], 0.99))
+        del amag
+        dt = 64.0 * (2.0 * eta * w.eps / q99) ** 0.5
+        rung = sr.assign_rungs(a32, dt, eta, w.eps)
+        rec["rung_histogram"] = torch.bincount(rung.long(), minlength=n_rung).tolist()
+        rng = np.random.default_rng(11)
+        k32 = np.sort(rng.choice(n, size=1 << 18, replace=False))
+        g32 = a32[:, torch.from_numpy(k32).to(dev)].double().cpu().numpy()
+        subs = {}
+        for lc in range(n_rung):
+            sr.build_pairs(None if lc == 0 else rung, lc)
+            sr.forces(p, 32, a32)
+            st = sr.stats()
+            subs[str(lc)] = {"receivers": st.n_active, "pairs": st.pairs_last,
+                             "force_kernel_ms": st.force_kernel_ms,
+                             "kernel_frac": st.pairs_last / (st.force_kernel_ms * 1e-3) / peak}
+        rec["rung_substeps"] = subs
+        # deepest-rung substep, FP32 and FP64 (receivers: rung 7; suppliers: all)
+        sr.build_pairs(rung, n_rung - 1)
+        sr.forces(p, 32, a32)
+        st32 = sr.stats()
+        a64 = torch.full((3, n), float("nan"), dtype=torch.float64, device=dev)
+        sr.forces(p, 64, a64)
+        st64 = sr.stats()
+        act = torch.nonzero(rung >= n_rung - 1).flatten()
+        gen.manual_seed(1)
+        k64 = torch.sort(act[torch.randperm(len(act), device=dev, generator=gen)[:1 << 18]]).values
+        g64 = a64[:, k64].cpu().numpy()
+        k64 = k64.cpu().numpy()
+        del a64
+        rec["deepest_rung"] = {
+            "rung": n_rung - 1, "receivers": st32.n_active, "pairs": st32.pairs_last,
+            "fp32_kernel_ms": st32.force_kernel_ms, "fp64_kernel_ms": st64.force_kernel_ms,
+            "fp32_value": st32.pairs_last / (st32.force_kernel_ms * 1e-3),
+            "fp64_value": st64.pairs_last / (st64.force_kernel_ms * 1e-3),
+            "fp32_over_fp64": st64.force_kernel_ms / st32.force_kernel_ms, "unit": UNIT}
+        perm_np = perm.cpu().numpy().astype(np.int64)
+        # the full step (sort with momenta and rungs carried, work list, FP32 forces,
+        # rungs + kick + drift), all particles receivers; FP32 momenta at 1024^3
+        mom = torch.zeros((3, n), dtype=torch.float32 if n > (1 << 28) else torch.float64, device=dev)
+        kick_factor = [dt / 2 ** l for l in range(n_rung)]
+        step_ms, step_pairs = [], []
+        for k in range(1 + steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sr.sort(p, carry=[mom, rung])
+            sr.build_pairs()
+            sr.forces(p, 32, a32)
+            sr.kick_drift(p, mom, a32, rung, dt, eta, w.eps, kick_factor, dt / 2 ** (n_rung - 1))
+            e1.record(stream)
+            st = sr.stats()
+            if k > 0:
+                step_ms.append(e0.elapsed_time(e1))
+                step_pairs.append(st.pairs_last)
+        rec["full_step"] = {"ms": statistics.mean(step_ms), "pairs": statistics.mean(step_pairs),
+                            "value": sum(step_pairs) / (sum(step_ms) * 1e-3), "unit": UNIT,
+                            "momenta": str(mom.dtype).replace("torch.", ""),
+                            "step": "sort+carry, work list, FP32 forces, rungs+kick+drift"}
+        del p, a32, mom, rung
+    torch.cuda.empty_cache()
+    if with_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        ref32, pc = oracle.sr_accel_subset(pos_np, perm_np[k32], w.x_s, w.x_r, w.G_m, "bspline", w.eps)
+        secs = time.perf_counter() - t0
+        ref64, _ = oracle.sr_accel_subset(pos_np, perm_np[k64], w.x_s, w.x_r, w.G_m, "bspline", w.eps)
+
+        def rel(a, b):
+            return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+        rec["cpu_baseline"] = {"value": float(pc.sum()) / secs, "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle",
+                               "sample": f"{len(k32)} seeded receivers of the initial state (all {n} suppliers; "
+                                         f"includes the cell-list build), {int(pc.sum())} pairs, {secs:.1f} s"}
+        rec["parity"] = {"receivers": len(k32), "fp32_all_active_rel_rms": rel(g32, ref32),
+                         "fp64_deepest_rung_rel_rms": rel(g64, ref64), "tolerance": {"fp32": 1e-5, "fp64": 1e-12}}
+    return rec
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -228,23 +363,29 @@ def run_ours(args):
     kick_factor = [dt / 2 ** l for l in range(n_rung)]
     drift_factor = dt / 2 ** (n_rung - 1)
 
-    def step():
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
         sr.sort(pos, carry=[mom, rung])
+        if ev is not None:
+            ev[1].record(stream)
         sr.build_pairs()
         sr.forces(pos, 32, acc)
-        sr.assign_rungs(acc, dt, eta, w.eps, rung)
-        sr.kick(mom, acc, kick_factor, rung, 0)
-        sr.drift(pos, mom, drift_factor)
+        if ev is not None:
+            ev[2].record(stream)
+        sr.kick_drift(pos, mom, acc, rung, dt, eta, w.eps, kick_factor, drift_factor)
+        if ev is not None:
+            ev[3].record(stream)
 
+    stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
-    stream = torch.cuda.current_stream(dev)
     vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip().isdigit()]
     sampler = ClockSampler(int(vis[local]) if local < len(vis) else local)
     launches0 = sr.stats().kernel_launches
-    step_ms, kern_ms, pairs = [], [], []
+    step_ms, kern_ms, pairs, sort_ms, kd_ms = [], [], [], [], []
     barrier(world)
     torch.cuda.synchronize()
     sampler.start()
@@ -252,13 +393,12 @@ def run_ours(args):
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        step(ev)
         st = sr.stats()  # synchronises the stream
-        step_ms.append(e0.elapsed_time(e1))
+        step_ms.append(ev[0].elapsed_time(ev[3]))
+        sort_ms.append(ev[0].elapsed_time(ev[1]))
+        kd_ms.append(ev[2].elapsed_time(ev[3]))
         kern_ms.append(st.force_kernel_ms)
         pairs.append(st.pairs_last)
     torch.cuda.synchronize()
@@ -289,6 +429,22 @@ def run_ours(args):
                 "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz / "
                               f"{OPS_PER_PAIR} FP32 ops per interacting pair",
                 "frac_of_each_pair_once_minimum": achieved / (2.0 * lane_rate / OPS_PER_PAIR_SYM)}
+
+    # HBM-bound phases of the step against the measured copy bandwidth
+    peak_gbs, peak_src = hbm_peak()
+
+    def hbm_rec(bytes_per_particle, ms_list, what):
+        ms = statistics.mean(ms_list)
+        gbs = bytes_per_particle * n / (ms * 1e-3) / 1e9
+        return {"what": what, "bytes_per_step": bytes_per_particle * n, "ms": ms, "gbs": gbs,
+                "frac": gbs / peak_gbs}
+    hbm = {"peak_gbs": peak_gbs, "peak_source": peak_src,
+           "sort": hbm_rec(SORT_BYTES_PER_PARTICLE, sort_ms,
+                           "p3m_sr_sort: bin, subtile offsets, stable radix sort, gathers of positions, "
+                           "momenta and rungs, FP32 records (algorithmic 110 B per particle)"),
+           "kick": hbm_rec(KICK_DRIFT_BYTES_PER_PARTICLE, kd_ms,
+                           "p3m_sr_kick_drift: Eq. rung, kick and drift in one pass (algorithmic 109 B per "
+                           "particle)")}
 
     # FP64 path and adjoint on the same (current) particle state
     sr.sort(pos, carry=[mom, rung])
@@ -410,7 +566,8 @@ def run_ours(args):
             ts.append(e0.elapsed_time(e1))
             tk.append(st.force_kernel_ms)
         rung_substeps[str(lc)] = {"receivers": st.n_active, "pairs": st.pairs_last,
-                                  "substep_ms": statistics.mean(ts), "force_kernel_ms": statistics.mean(tk)}
+                                  "substep_ms": statistics.mean(ts), "force_kernel_ms": statistics.mean(tk),
+                                  "kernel_frac": st.pairs_last / (statistics.mean(tk) * 1e-3) / peak}
     # one global step of the full rung cycle (2^(n_rung-1) substeps, synchronised at its end)
     from paper_2112_01508_gb300.integrate import rung_leapfrog
 
@@ -494,9 +651,7 @@ def run_ours(args):
         sr.sort(P[i], carry=[Q[i], R[i]])
         sr.build_pairs()
         sr.forces(P[i], 32, A[i])
-        sr.assign_rungs(A[i], dt, eta, w.eps, R[i])
-        sr.kick(Q[i], A[i], kick_factor, R[i], 0)
-        sr.drift(P[i], Q[i], drift_factor)
+        sr.kick_drift(P[i], Q[i], A[i], R[i], dt, eta, w.eps, kick_factor, drift_factor)
 
     e_start = torch.cuda.Event(enable_timing=True)
     e_end = torch.cuda.Event(enable_timing=True)
@@ -543,6 +698,13 @@ def run_ours(args):
                                "sample": f"{nrecv1} seeded receivers, {cp1} pairs, {secs1:.1f} s"}}
 
     sr.close()
+    del flush, P, Q, R, A, pos0, acc64
+    torch.cuda.empty_cache()
+    large = {}
+    if world == 1 and not args.no_large:
+        for name in ("n134m", "n1g"):
+            large[name] = large_record(name, dev, rank == 0 and not args.no_cpu_baseline)
+            torch.cuda.empty_cache()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -550,7 +712,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{w.name}: {w.description}", "n": n, "n_sub": w.n_sub,
                        "softening": "bspline", "precision": "fp32 forces, fp64 positions/kicks",
-                       "step": "sort+carry, work list, FP32 forces, rungs, kick, drift (all active)",
+                       "step": "sort+carry, work list, FP32 forces, rungs+kick+drift (one pass; all active)",
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "pairs_per_step": pairs_avg,
@@ -567,7 +729,9 @@ def run_ours(args):
             "subtile_refinement": refinement,
             "rung_substeps": rung_substeps,
             "rung_cycle": rung_cycle,
+            "large_workloads": large,
             "roofline": roofline,
+            "hbm": hbm,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * 8 * n,
                     "d2h_bytes_per_step": 3 * 4 * n, "ms_per_step": e2e_total / args.steps,

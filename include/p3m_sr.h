@@ -138,7 +138,8 @@ p3m_status p3m_sr_set_subtiles(p3m_sr_ctx* ctx, const int* n_sub);
  * tiles, memory reordered in tile -> subtile -> particle walk order).
  *   pos          3 x n float64 SoA, device; reordered IN PLACE.  Each position
  *                must be finite and in [0, L) (else P3M_ERR_NONFINITE is
- *                latched and the particle is binned at the clamped cell).
+ *                latched, the offending coordinate is binned as 0 and the
+ *                forces that follow are undefined until the next good sort).
  *   carry        n_carry device arrays of n elements of carry_bytes[c] bytes
  *                each (1..32), permuted in place alongside (momenta, rungs,
  *                identifiers ...).  May be NULL when n_carry == 0.
@@ -298,6 +299,25 @@ p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom, int mom_p
                         double factor);
 
 /*
+ * Rungs, kick and drift in one pass over the particle arrays (Section 2.2.2:
+ * Eq. rung, then operator K, then operator D, with a = 1), for steps in which
+ * every particle is kicked: for each particle,
+ *   rung_i <- Eq. rung of a_i            (as p3m_sr_assign_rungs),
+ *   q_i    <- q_i + a_i kick_factor[rung_i]   (as p3m_sr_kick with rung_min 0),
+ *   x_i    <- wrap(x_i + q_i drift_factor)   (as p3m_sr_drift),
+ * with the same IEEE double arithmetic, so the results equal those three calls
+ * bit for bit while the arrays are read and written once.
+ *   pos        3 x n float64 device; mom 3 x n device (mom_precision 32 or 64);
+ *   acc        3 x n device (acc_precision 32 or 64); rung_out n int8 device;
+ *   kick_factor HOST array of n_rung doubles; drift_factor finite.
+ * Drifting the array of the last p3m_sr_sort keeps that sort usable exactly as
+ * p3m_sr_drift does.  Non-finite accelerations latch P3M_ERR_NONFINITE.
+ */
+p3m_status p3m_sr_kick_drift(p3m_sr_ctx* ctx, double* pos, void* mom, int mom_precision, const void* acc,
+                             int acc_precision, int8_t* rung_out, double dt, double eta, double eps,
+                             const double* kick_factor, double drift_factor);
+
+/*
  * Vector-Jacobian product of the short-range accelerations with respect to
  * the positions (derived from Eq. p3m_gravity):
  *   xbar_k = sum_{j != k, r_kj < x_r} J_kj (abar_k [k active] - abar_j [j active]),
@@ -326,21 +346,26 @@ p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precision, const v
  * receiver chunks and evaluates the FP32 forces with the same kernels as
  * p3m_sr_sort + p3m_sr_build_pairs + p3m_sr_forces (all particles active), but
  * keeps every intermediate array in one fixed-size device array inside the
- * library (about 6 MB, held by every GPU that loads the library until the
+ * library (about 7.6 MB, held by every GPU that loads the library until the
  * process exits).
  *   params      as for p3m_sr_create; n <= 65536, at most 2^18 subtiles and
  *               2^14 chunk segments (n_t^2 ceil(n_t/4)), x_r <= 4.6 x_s.  Larger inputs return
  *               P3M_ERR_INVALID.
  *   cuda_stream cudaStream_t; all work is enqueued on it (nothing is waited for).
- *   pos         3 x n float64 SoA, device, any order, each coordinate in
- *               [0, L); it is not modified.  Positions outside the box are
- *               clamped into it without an error report.
+ *   pos         3 x n float64 SoA, device, any order; it is not modified.
+ *               The box is periodic: a finite coordinate outside [0, L) is
+ *               taken as its periodic image x - L floor(x / L).  A particle
+ *               with a non-finite coordinate gets NaN accelerations and exerts
+ *               no force on the others (no status reports it: the call does
+ *               not wait for the GPU).
  *   acc_out     3 x n float, device: accelerations in the order of pos.
  * The first call on a device looks up the device address of the internal array
  * (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture.  Every call uses the same internal array: calls whose GPU
- * work overlaps (other streams, other host threads) race and must be
- * serialised by the caller.
+ * any stream capture.  The address is kept for the life of the process: do not
+ * use this entry point on a device after cudaDeviceReset (or any other
+ * teardown of its primary context).  Every call uses the same internal array:
+ * calls whose GPU work overlaps (other streams, other host threads) race and
+ * must be serialised by the caller.
  */
 p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* cuda_stream, const double* pos,
                                  float* acc_out);

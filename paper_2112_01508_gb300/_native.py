@@ -34,7 +34,7 @@ EXPORTS = (
     "p3m_sr_create", "p3m_sr_destroy", "p3m_sr_last_error", "p3m_sr_sync", "p3m_sr_stats", "p3m_sr_sort",
     "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
     "p3m_sr_permute", "p3m_sr_unpermute", "p3m_sr_forces_noalloc", "p3m_sr_forces_tabulated",
-    "p3m_sr_rung_kick", "p3m_sr_set_subtiles", "p3m_sr_set_symmetric",
+    "p3m_sr_rung_kick", "p3m_sr_set_subtiles", "p3m_sr_set_symmetric", "p3m_sr_kick_drift",
 )
 
 
@@ -114,6 +114,8 @@ def load() -> ctypes.CDLL:
         L.p3m_sr_kick.restype = i
         L.p3m_sr_drift.argtypes = [p, p, p, i, d]
         L.p3m_sr_drift.restype = i
+        L.p3m_sr_kick_drift.argtypes = [p, p, p, i, p, i, p, d, d, d, ctypes.POINTER(d), d]
+        L.p3m_sr_kick_drift.restype = i
         L.p3m_sr_vjp.argtypes = [p, p, i, p, p]
         L.p3m_sr_vjp.restype = i
         L.p3m_sr_permute.argtypes = [p, p, p, i, i]
@@ -199,6 +201,14 @@ def p3m_sr_kick(ctx, mom_ptr, mom_precision, acc_ptr, acc_precision, rung_ptr, r
 def p3m_sr_drift(ctx, pos_ptr, mom_ptr, mom_precision, factor) -> int:
     return load().p3m_sr_drift(ctx, ctypes.c_void_p(pos_ptr), ctypes.c_void_p(mom_ptr), int(mom_precision),
                                float(factor))
+
+
+def p3m_sr_kick_drift(ctx, pos_ptr, mom_ptr, mom_precision, acc_ptr, acc_precision, rung_ptr, dt, eta, eps,
+                      kick_factor, drift_factor) -> int:
+    kf = (ctypes.c_double * len(kick_factor))(*[float(k) for k in kick_factor])
+    return load().p3m_sr_kick_drift(ctx, ctypes.c_void_p(pos_ptr), ctypes.c_void_p(mom_ptr), int(mom_precision),
+                                    ctypes.c_void_p(acc_ptr), int(acc_precision), ctypes.c_void_p(rung_ptr),
+                                    float(dt), float(eta), float(eps), kf, float(drift_factor))
 
 
 def p3m_sr_vjp(ctx, pos_ptr, precision, acc_bar_ptr, pos_bar_ptr) -> int:

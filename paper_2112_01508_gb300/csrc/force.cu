@@ -1838,7 +1838,9 @@ struct NoallocLayout {
   static constexpr int64_t offsets = vals1 + noalloc_align(4 * kNoallocMaxN);
   static constexpr int64_t hist = offsets + noalloc_align(4 * (kNoallocMaxSubtiles + 1));
   static constexpr int64_t scan = hist + noalloc_align(4 * 1024 * kNoallocRadixBlocks);
-  static constexpr int64_t pos = scan + noalloc_align(4 * 4096);
+  static constexpr int64_t wpos = scan + noalloc_align(4 * 4096);
+  static constexpr int64_t bad = wpos + noalloc_align(8 * 3 * kNoallocMaxN);
+  static constexpr int64_t pos = bad + noalloc_align(kNoallocMaxN);
   static constexpr int64_t rel4 = pos + noalloc_align(8 * 3 * kNoallocMaxN);
   static constexpr int64_t rows = rel4 + noalloc_align(16 * kNoallocMaxN);
   static constexpr int64_t chunks = rows + noalloc_align(4 * (kNoallocMaxRows + 1));
@@ -1853,15 +1855,65 @@ constexpr int kNoallocMaxDevices = 64;
 static void* g_noalloc_addr[kNoallocMaxDevices];
 static std::mutex g_noalloc_mutex;
 
-// acc_out[d][perm[k]] = acc[d][k]
-__global__ void k_noalloc_unsort(const float* __restrict__ acc, const int* __restrict__ perm, int64_t n,
-                                 float* __restrict__ out) {
+// The caller's positions brought into the periodic box: x - L floor(x / L) for a
+// finite coordinate outside [0, L) (the same point of the periodic box), 0 with
+// bad[i] = 1 for a non-finite one.
+__global__ void k_noalloc_wrap(const double* __restrict__ pos, int64_t n, double box, double* __restrict__ wpos,
+                               unsigned char* __restrict__ bad) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool finite = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = pos[d * n + i];
+    if (!isfinite(v)) {
+      finite = false;
+      v = 0.0;
+    } else if (!(v >= 0.0 && v < box)) {
+      v = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
+      if (!(v >= 0.0 && v < box)) v = 0.0;  // rounded up to L: the same point as 0
+    }
+    if (v == 0.0) v = 0.0;  // -0 as +0 (the binning compares bit patterns)
+    wpos[d * n + i] = v;
+  }
+  bad[i] = finite ? 0 : 1;
+}
+
+// Sorted positions and FP32 subtile-relative records; a particle with a
+// non-finite coordinate gets a record far outside the box, so that no receiver
+// ever meets it (its own row is overwritten with NaN by k_noalloc_unsort).
+__global__ void k_noalloc_gather(const double* __restrict__ wpos, const unsigned char* __restrict__ bad,
+                                 const int* __restrict__ perm, const int* __restrict__ cell, int64_t n, Geometry g,
+                                 double* __restrict__ spos, float4* __restrict__ rel4) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int64_t j = perm[k];
+  const double x = wpos[j], y = wpos[n + j], z = wpos[2 * n + j];
+  spos[k] = x;
+  spos[n + k] = y;
+  spos[2 * n + k] = z;
+  const int id = cell[k];
+  if (bad[j]) {
+    rel4[k] = make_float4(1e10f, 1e10f, 1e10f, __int_as_float(id));
+    return;
+  }
+  int gx, gy, gz;
+  decode_subtile(g, id, gx, gy, gz);
+  rel4[k] = make_float4((float)__fma_rn(-(double)gx, g.side64[0], x), (float)__fma_rn(-(double)gy, g.side64[1], y),
+                        (float)__fma_rn(-(double)gz, g.side64[2], z), __int_as_float(id));
+}
+
+// acc_out[d][perm[k]] = acc[d][k], NaN for a particle with a non-finite coordinate
+__global__ void k_noalloc_unsort(const float* __restrict__ acc, const int* __restrict__ perm,
+                                 const unsigned char* __restrict__ bad, int64_t n, float* __restrict__ out) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int64_t j = perm[k];
-  out[j] = acc[k];
-  out[n + j] = acc[n + k];
-  out[2 * n + j] = acc[2 * n + k];
+  const float nan = __int_as_float(0x7fc00000);
+  const bool b = bad[j] != 0;
+  out[j] = b ? nan : acc[k];
+  out[n + j] = b ? nan : acc[n + k];
+  out[2 * n + j] = b ? nan : acc[2 * n + k];
 }
 
 }  // namespace p3m
@@ -1908,20 +1960,25 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
   int* offsets = (int*)(base + Lay::offsets);
   int* hist = (int*)(base + Lay::hist);
   int* scan = (int*)(base + Lay::scan);
+  double* wpos = (double*)(base + Lay::wpos);
+  unsigned char* bad = base + Lay::bad;
   double* spos = (double*)(base + Lay::pos);
   float4* rel4 = (float4*)(base + Lay::rel4);
   int* rows = (int*)(base + Lay::rows);
   Chunk* chunks = (Chunk*)(base + Lay::chunks);
   float* acc = (float*)(base + Lay::acc);
-  int* small = (int*)(base + Lay::small);  // [0] n_chunks, [1] counter, [2] error bits, [4..5] pair count
+  int* small = (int*)(base + Lay::small);  // [0] n_chunks, [1] counter, [2] k_bin's error word (unused: the
+                                           // positions are wrapped first), [4..5] pair count
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int64_t launches = 0;
   auto ok = [&](cudaError_t e) { return e == cudaSuccess; };
 
-  // bin + subtile offsets (histogram, exclusive scan)
+  // periodic wrap, then bin + subtile offsets (histogram, exclusive scan)
   if (!ok(cudaMemsetAsync(offsets, 0, sizeof(int) * (g.S + 1), s))) return P3M_ERR_CUDA;
   if (!ok(cudaMemsetAsync(small, 0, 64, s))) return P3M_ERR_CUDA;
-  k_bin<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, g, keys[0], vals[0], offsets, small + 2);
+  k_noalloc_wrap<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, g.box, wpos, bad);
+  if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
+  k_bin<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(wpos, n, g, keys[0], vals[0], offsets, small + 2);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   if (!ok(scan_exclusive_i32(offsets, offsets, g.S + 1, scan, s, &launches))) return P3M_ERR_CUDA;
   // stable LSD radix sort of the subtile ids
@@ -1945,8 +2002,8 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
   const int* cell = keys[cur];
   const int* perm = vals[cur];
   // sorted positions and their FP32 subtile-relative records
-  k_gather_pos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, perm, n, spos);
-  k_rel4<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(spos, cell, n, g, rel4);
+  k_noalloc_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(wpos, bad, perm, cell, n, g, spos, rel4);
+  if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   // receiver chunks (all particles active)
   const int64_t nrows = (int64_t)g.n_t * g.n_t * ((g.n_t + kChunkSpan - 1) / kChunkSpan);  // segments
   k_row_chunks<<<(unsigned)((nrows + 1 + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows);
@@ -1981,7 +2038,7 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
     default: k_force_packed<P3M_SOFT_BSPLINE><<<grid, kPThreads, 0, s>>>(a); break;
   }
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
-  k_noalloc_unsort<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, perm, n, acc_out);
+  k_noalloc_unsort<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, perm, bad, n, acc_out);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   return P3M_OK;
 }

@@ -132,6 +132,53 @@ __global__ void __launch_bounds__(256) k_drift(double* __restrict__ pos, const M
   }
 }
 
+// Rungs (Eq. rung), kick and drift in one pass over the particle arrays: the
+// arithmetic of k_rungs, k_kick (rung_min 0) and k_drift in that order, so the
+// results are those of the three kernels bit for bit.  disp as in k_drift.
+template <class M, class A>
+__global__ void __launch_bounds__(256) k_kick_drift(double* __restrict__ pos, M* __restrict__ mom,
+                                                    const A* __restrict__ acc, int8_t* __restrict__ rung, int64_t n,
+                                                    double qq, float qqf, int n_rung, KickFactors kf, double factor,
+                                                    double box, float* __restrict__ disp, int* __restrict__ err) {
+  __shared__ unsigned warp_max[8];
+  float my = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const A av[3] = {acc[i], acc[n + i], acc[2 * n + i]};
+    const int l = rung_rule<A>(av[0], av[1], av[2], qq, qqf, n_rung, err);
+    rung[i] = (int8_t)l;
+    const double k = kf.k[l];
+    float q2 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const M qm = (M)__dadd_rn((double)mom[d * n + i], __dmul_rn((double)av[d], k));
+      mom[d * n + i] = qm;
+      const double q = (double)qm;
+      const float qf = (float)q;
+      q2 = fmaf(qf, qf, q2);
+      double v = __dadd_rn(pos[d * n + i], __dmul_rn(q, factor));
+      const long long vb = __double_as_longlong(v);
+      if (!(vb >= 0 && vb < __double_as_longlong(box))) {
+        v = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
+        if (v >= box || v < 0.0) v = 0.0;
+      }
+      pos[d * n + i] = v;
+    }
+    float di = sqrtf(q2) * (float)fabs(factor) * 1.0001f;
+    if (!(di < 3.0e38f)) di = 3.0e38f;
+    my = fmaxf(my, di);
+  }
+  if (disp) {
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(my));
+    if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned b = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = max(b, warp_max[w]);
+      if (b) atomicMax((unsigned*)disp, b);
+    }
+  }
+}
+
 // One kick of the rung-based leapfrog with the rung update (see p3m_sr_rung_kick).
 template <class M, class A>
 __global__ void k_rung_kick(M* __restrict__ mom, const A* __restrict__ acc, int8_t* __restrict__ rung,
@@ -173,9 +220,80 @@ __global__ void k_rung_kick(M* __restrict__ mom, const A* __restrict__ acc, int8
   state[i] = (int8_t)ost;
 }
 
+// Drifting the sorted positions keeps the sort usable: the displacement bound of
+// each drift is recorded and the pair traversal widens its reach by their sum,
+// until kMaxDrifts drifts, after which a new sort is required.  Returns the slot
+// that receives this drift's bound (nullptr when pos is not the sorted array).
+static float* drift_slot(p3m_sr_ctx* ctx, const double* pos) {
+  float* slot = nullptr;
+  if (ctx->sorted && pos == ctx->sorted_pos) {
+    if (ctx->n_drift < kMaxDrifts) {
+      slot = ctx->drift_slots + ctx->n_drift++;
+      ctx->rel4_stale = true;
+    } else {
+      ctx->sorted = false;
+      ctx->pairs_built = false;
+      ctx->sorted_pos = nullptr;
+    }
+  }
+  return slot;
+}
+
+// q = dt^2 / (2 eta eps) in this order in IEEE double, then qq = q^2 (Eq. rung)
+static double rung_qq(double dt, double eta, double eps) {
+  volatile double t1 = dt * dt;
+  volatile double t2 = 2.0 * eta;
+  volatile double t3 = t2 * eps;
+  volatile double q = t1 / t3;
+  return q * q;
+}
+
 }  // namespace p3m
 
 using namespace p3m;
+
+extern "C" p3m_status p3m_sr_kick_drift(p3m_sr_ctx* ctx, double* pos, void* mom, int mom_precision, const void* acc,
+                                       int acc_precision, int8_t* rung_out, double dt, double eta, double eps,
+                                       const double* kick_factor, double drift_factor) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if ((mom_precision != 32 && mom_precision != 64) || (acc_precision != 32 && acc_precision != 64))
+    return fail(ctx, P3M_ERR_INVALID, "kick_drift: precision must be 32 or 64");
+  if (!kick_factor) return fail(ctx, P3M_ERR_INVALID, "kick_drift: null kick_factor");
+  if (ctx->n > 0 && (!pos || !mom || !acc || !rung_out)) return fail(ctx, P3M_ERR_INVALID, "kick_drift: null pointer");
+  if (!(dt >= 0.0) || !(eta > 0.0) || !(eps > 0.0))
+    return fail(ctx, P3M_ERR_INVALID, "kick_drift: need dt >= 0, eta > 0, eps > 0");
+  if (!std::isfinite(drift_factor)) return fail(ctx, P3M_ERR_INVALID, "kick_drift: drift_factor must be finite");
+  p3m_status st = poll_latched(ctx);
+  if (st != P3M_OK) return st;
+  if (ctx->n == 0) return P3M_OK;
+  const double qq = rung_qq(dt, eta, eps);
+  KickFactors kf{};
+  for (int l = 0; l < ctx->prm.n_rung; ++l) kf.k[l] = kick_factor[l];
+  float* slot = drift_slot(ctx, pos);
+  const int t = 256;
+  const int64_t n = ctx->n;
+  const unsigned b = (unsigned)std::min<int64_t>(blocks_for(n, t), (int64_t)ctx->num_sms * 8);
+  cudaStream_t s = ctx->stream;
+  const int nr = ctx->prm.n_rung;
+  const double L = ctx->prm.box;
+  const float qqf = rung_qqf(qq);
+  if (mom_precision == 64 && acc_precision == 32)
+    k_kick_drift<double, float><<<b, t, 0, s>>>(pos, (double*)mom, (const float*)acc, rung_out, n, qq, qqf, nr, kf,
+                                                drift_factor, L, slot, ctx->err_dev);
+  else if (mom_precision == 64 && acc_precision == 64)
+    k_kick_drift<double, double><<<b, t, 0, s>>>(pos, (double*)mom, (const double*)acc, rung_out, n, qq, qqf, nr, kf,
+                                                 drift_factor, L, slot, ctx->err_dev);
+  else if (mom_precision == 32 && acc_precision == 32)
+    k_kick_drift<float, float><<<b, t, 0, s>>>(pos, (float*)mom, (const float*)acc, rung_out, n, qq, qqf, nr, kf,
+                                               drift_factor, L, slot, ctx->err_dev);
+  else
+    k_kick_drift<float, double><<<b, t, 0, s>>>(pos, (float*)mom, (const double*)acc, rung_out, n, qq, qqf, nr, kf,
+                                                drift_factor, L, slot, ctx->err_dev);
+  ++ctx->launches;
+  if ((st = cuda_check(ctx, cudaGetLastError(), "kick-drift kernel")) != P3M_OK) return st;
+  report_latched(ctx);
+  return P3M_OK;
+}
 
 extern "C" p3m_status p3m_sr_assign_rungs(p3m_sr_ctx* ctx, const void* acc, int acc_precision, double dt, double eta,
                                           double eps, int8_t* rung_out) {
@@ -243,20 +361,7 @@ extern "C" p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom
   p3m_status st = poll_latched(ctx);
   if (st != P3M_OK) return st;
   if (ctx->n == 0) return P3M_OK;
-  // Drifting the sorted positions keeps the sort usable: the displacement bound of
-  // each drift is recorded and the pair traversal widens its reach by their sum,
-  // until kMaxDrifts drifts, after which a new sort is required.
-  float* slot = nullptr;
-  if (ctx->sorted && pos == ctx->sorted_pos) {
-    if (ctx->n_drift < kMaxDrifts) {
-      slot = ctx->drift_slots + ctx->n_drift++;
-      ctx->rel4_stale = true;
-    } else {
-      ctx->sorted = false;
-      ctx->pairs_built = false;
-      ctx->sorted_pos = nullptr;
-    }
-  }
+  float* slot = drift_slot(ctx, pos);
   const int t = 256;
   const unsigned b = blocks_for(ctx->n, t);
   if (mom_precision == 64)

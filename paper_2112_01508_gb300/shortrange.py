@@ -202,6 +202,21 @@ class ShortRange:
         _check(mom, "mom", (torch.float32, torch.float64), (3, self.n), self.device)
         self._raise(nat.p3m_sr_drift(self._ctx, pos.data_ptr(), mom.data_ptr(), _PREC[mom.dtype], factor))
 
+    def kick_drift(self, pos: torch.Tensor, mom: torch.Tensor, acc: torch.Tensor, rung_out: torch.Tensor,
+                   dt: float, eta: float, eps: float, kick_factor, drift_factor: float):
+        """Rungs (Eq. rung), kick and drift in one pass (p3m_sr_kick_drift): the results of
+        assign_rungs + kick(rung_min=0) + drift, bit for bit."""
+        _check(pos, "pos", torch.float64, (3, self.n), self.device)
+        _check(mom, "mom", (torch.float32, torch.float64), (3, self.n), self.device)
+        _check(acc, "acc", (torch.float32, torch.float64), (3, self.n), self.device)
+        _check(rung_out, "rung_out", torch.int8, (self.n,), self.device)
+        kf = [float(k) for k in kick_factor]
+        if len(kf) < self.n_rung:
+            kf = kf + [kf[-1]] * (self.n_rung - len(kf))
+        self._raise(nat.p3m_sr_kick_drift(self._ctx, pos.data_ptr(), mom.data_ptr(), _PREC[mom.dtype],
+                                          acc.data_ptr(), _PREC[acc.dtype], rung_out.data_ptr(), dt, eta, eps, kf,
+                                          drift_factor))
+
     def vjp(self, pos: torch.Tensor, acc_bar: torch.Tensor, precision: int | None = None,
             out: torch.Tensor | None = None) -> torch.Tensor:
         _check(pos, "pos", torch.float64, (3, self.n), self.device)

@@ -101,3 +101,33 @@ def test_header_documents_every_entry_point():
     for name in nat.EXPORTS:
         assert name in text
     assert "Section 2.1.3" in text and "Eq. rung" in text
+
+
+def _noalloc_params(**kw):
+    """32^3-recipe parameters (x_s = 1.25/64, x_r = 4.5 x_s, 11 tiles per dimension)."""
+    x_s = 1.25 / 64
+    return _params(**{**dict(n=1 << 15, x_s=x_s, x_r=4.5 * x_s, eps=0.03 / 32), **kw})
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n=(1 << 16) + 1),                                     # beyond the particle limit
+    dict(n_sub=(6, 6, 6)),                                     # (11 * 6)^3 = 287,496 subtiles > 2^18
+    dict(x_r=1.0 / 41.5, x_s=1.0 / 41.5 / 4.5, eps=1e-4, n_sub=(1, 1, 1)),  # 41^2 ceil(41/4) = 18,491 segments > 2^14
+    dict(x_s=1.25 / 64 * 0.9),                                 # x_r = 5 x_s: beyond the FP32 erfc fit
+    dict(n=-1),
+    dict(x_r=0.3),                                             # fewer than 4 tiles
+])
+def test_forces_noalloc_rejects_inputs_beyond_its_limits(kw):
+    # every limit is checked on the host before any device call, so this runs without a GPU
+    lib = nat.load()
+    p = _noalloc_params(**kw)
+    st = lib.p3m_sr_forces_noalloc(ctypes.byref(p), None, None, None)
+    assert st in (nat.P3M_ERR_INVALID, nat.P3M_ERR_TOO_FEW_TILES)
+
+
+def test_forces_noalloc_limits_admit_the_largest_sets():
+    # at the limits (n = 2^16, 2^18 subtiles would need n_sub = 5.8; n_sub = 5 gives
+    # 166,375) an empty particle set is accepted without touching the device
+    lib = nat.load()
+    p = _noalloc_params(n=0, n_sub=(5, 5, 5))
+    assert lib.p3m_sr_forces_noalloc(ctypes.byref(p), None, None, None) == nat.P3M_OK

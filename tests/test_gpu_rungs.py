@@ -162,11 +162,22 @@ def test_rung_kick_bitexact(mom_dt, acc_dt, k, sync):
         assert (got_r != rung).any()  # some particles jumped
 
 
+# FP32 rung cycle against the FP64 oracle cycle (the bounds below are derived in the
+# design notes, reading "FP32 rung cycle"):
+FP32_CYCLE_MAX_RUNG_CHANGES = 4   # particles whose rung history may differ (0.1% of 4096)
+FP32_CYCLE_DX = 1e-4              # per-particle |dx| / largest displacement of the oracle cycle
+FP32_CYCLE_DQ = 2e-4              # per-particle |dq| / largest momentum of the oracle cycle
+FP32_CYCLE_RMS = 1e-5             # relative RMS of displacements and momenta
+
+
 def test_rung_leapfrog_fp32_momenta_vs_oracle():
     """FP32 momenta (stored once rounded after each FP64 kick) and FP32 forces: the
-    cycle stays within FP32 rounding of the FP64 oracle cycle.  A particle whose
-    acceleration sits within FP32 rounding of a rung boundary may take another rung
-    (and kick schedule): such particles are counted, not compared."""
+    cycle stays within FP32 rounding, grown by the dynamics, of the FP64 oracle cycle.
+
+    A particle whose FP32 acceleration lies within FP32 rounding of a power-of-16
+    boundary of Eq. rung may take the other rung (and kick schedule); there may be at
+    most FP32_CYCLE_MAX_RUNG_CHANGES such particles, and they and their neighbours
+    (which met them on another trajectory) are left out of the per-particle bounds."""
     n, eta, eps, n_rung, n_steps = 4096, 0.025, W.eps, 4, 2
     pos = _subset(n, 11)
     dt = _dt_for_rungs(pos, eta, eps)
@@ -193,11 +204,24 @@ def test_rung_leapfrog_fp32_momenta_vs_oracle():
         h = np.empty(n, np.int8)
         h[o_gpu.cpu().numpy().astype(np.int64)] = h_gpu.cpu().numpy()
         same &= h == h_ref
-    assert same.mean() > 0.999
-    # displacements from the start, compared as a relative RMS like the forces
+    changed = np.flatnonzero(~same)
+    assert len(changed) <= FP32_CYCLE_MAX_RUNG_CHANGES, len(changed)
     d_got = got_p - pos
     d_got -= np.round(d_got)
     d_ref = p_ref - pos
     d_ref -= np.round(d_ref)
-    assert rel_rms(d_got[:, same], d_ref[:, same]) <= 1e-5
-    assert rel_rms(got_q[:, same], q_ref[:, same]) <= 1e-5
+    X = np.linalg.norm(d_ref, axis=0).max()
+    Q = np.linalg.norm(q_ref, axis=0).max()
+    # neighbours of a particle on another rung history: within x_r + 2X of it at the start
+    clean = same.copy()
+    for c in changed:
+        dd = pos - pos[:, c:c + 1]
+        dd -= np.round(dd)
+        clean &= np.sqrt((dd ** 2).sum(axis=0)) >= W.x_r + 2 * X
+    assert clean.sum() >= n - 129 * len(changed)
+    dx = np.linalg.norm(d_got - d_ref, axis=0)
+    dq = np.linalg.norm(got_q - q_ref, axis=0)
+    assert dx[clean].max() <= FP32_CYCLE_DX * X, dx[clean].max() / X
+    assert dq[clean].max() <= FP32_CYCLE_DQ * Q, dq[clean].max() / Q
+    assert rel_rms(d_got[:, clean], d_ref[:, clean]) <= FP32_CYCLE_RMS
+    assert rel_rms(got_q[:, clean], q_ref[:, clean]) <= FP32_CYCLE_RMS

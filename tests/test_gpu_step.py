@@ -110,6 +110,68 @@ def test_drift_bitexact(mom_dt):
     np.testing.assert_array_equal(p.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("mom_dt,acc_dt", [(np.float64, np.float32), (np.float64, np.float64),
+                                           (np.float32, np.float32), (np.float32, np.float64)])
+def test_kick_drift_bitexact(mom_dt, acc_dt):
+    """The fused pass equals Eq. rung + kick + drift of the oracle, bit for bit, and
+    the three separate entry points."""
+    n = 60000
+    rng = np.random.default_rng(9)
+    pos = rng.random((3, n))
+    pos[:, :50] = rng.choice([1e-17, 1.0 - 1e-16, 0.5], size=(3, 50))  # wraps at both faces
+    mag = np.exp(rng.uniform(np.log(1e-3), np.log(1e6), n))
+    acc = rng.normal(size=(3, n))
+    acc = (acc * mag / np.linalg.norm(acc, axis=0)).astype(acc_dt)
+    mom = rng.normal(size=(3, n)).astype(mom_dt)
+    dt, eta, eps, drift = 0.0123, 0.025, W1.eps, 0.0731
+    kf = [dt / 2 ** l for l in range(8)]
+    rung_ref, bad = oracle.rungs(acc.astype(np.float64), dt, eta, eps, 8)
+    assert bad == 0 and len(np.unique(rung_ref)) >= 5
+    q_ref = oracle.kick(mom.astype(np.float64), acc.astype(np.float64), kf, rung=rung_ref, rung_min=0)
+    q_ref = q_ref.astype(mom_dt)
+    p_ref = oracle.drift(pos, q_ref.astype(np.float64), drift)
+    with _ctx(n) as sr:
+        p = torch.from_numpy(pos.copy()).cuda()
+        m = torch.from_numpy(mom.copy()).cuda()
+        a = torch.from_numpy(acc).cuda()
+        r = torch.empty(n, dtype=torch.int8, device="cuda")
+        sr.kick_drift(p, m, a, r, dt, eta, eps, kf, drift)
+        # the same three steps as separate calls
+        p2 = torch.from_numpy(pos.copy()).cuda()
+        m2 = torch.from_numpy(mom.copy()).cuda()
+        r2 = sr.assign_rungs(a, dt, eta, eps)
+        sr.kick(m2, a, kf, r2, 0)
+        sr.drift(p2, m2, drift)
+        sr.sync()
+    np.testing.assert_array_equal(r.cpu().numpy(), rung_ref)
+    np.testing.assert_array_equal(m.cpu().numpy(), q_ref)
+    np.testing.assert_array_equal(p.cpu().numpy(), p_ref)
+    assert torch.equal(r, r2) and torch.equal(m, m2) and torch.equal(p, p2)
+
+
+def test_kick_drift_keeps_the_sort_usable():
+    """Forces after a fused kick-drift of the sorted positions (no new sort) equal the
+    forces after a fresh sort: the pass records its displacement bound like a drift."""
+    pos = synth.workload_positions(W1)
+    n = W1.n
+    with _ctx(n) as sr:
+        p = torch.from_numpy(pos.copy()).cuda()
+        sr.sort(p)
+        sr.build_pairs()
+        a = sr.forces(p, 64)
+        m = torch.zeros((3, n), dtype=torch.float64, device="cuda")
+        r = torch.empty(n, dtype=torch.int8, device="cuda")
+        dt = 0.02
+        sr.kick_drift(p, m, a, r, dt, 0.025, W1.eps, [dt / 2 ** l for l in range(8)], dt)
+        sr.build_pairs()
+        got = sr.forces(p, 64).cpu().numpy()
+        pairs = sr.stats().pairs_last
+        moved = p.cpu().numpy()
+    ref, ref_pairs = oracle.sr_accel(moved, W1.x_s, W1.x_r, W1.G_m, "bspline", W1.eps)
+    assert pairs == ref_pairs
+    assert rel_rms(got, ref) <= 1e-12
+
+
 def test_permute_roundtrip():
     pos = synth.workload_positions(W1)
     n = W1.n
