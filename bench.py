@@ -49,6 +49,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["replicas", "slabs"], default="replicas",
+                    help="N > 1: independent replicas (weak scaling) or the slab decomposition of one set "
+                         "with halo exchange (strong scaling)")
     ap.add_argument("--workload", default="n2m")
     ap.add_argument("--cpu-sample", type=int, default=1 << 18, help="receivers in the CPU-oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1 << 14, help="receivers per reference-arm step")
@@ -56,7 +59,7 @@ def parse_args():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 512^3 and 1024^3 sub-records (full step, rung substeps, FP32 vs FP64)")
     ap.add_argument("--only", choices=["forces32", "forces32_gather", "forces64", "vjp32", "sort", "pm32",
-                                       "rung_steps"],
+                                       "rung_steps", "kick"],
                     default=None,
                     help="profiling mode: run just one kernel family (no contract line)")
     return ap.parse_args()
@@ -622,6 +625,42 @@ def run_ours(args):
         refinement = {"start_n_sub": 1, "final_n_sub": ref.current[0], "force_calls": 64, "interval": 16,
                       "trials": [{"n_sub": e[1][0], "record_ps_per_pair": e[2] * 1e9,
                                   "trial_ps_per_pair": e[3] * 1e9, "kept": e[4]} for e in ref.log.events]}
+    # per-region refinement: 4 slab regions of the box, each with its own subtiles per
+    # tile chosen by the same timed trial rule (Section 2.1.3, "Subtiles": per domain),
+    # against every region at a uniform n_sub = 1 ... 4 in the same pipeline
+    from paper_2112_01508_gb300.refine import RegionRefiner
+    from paper_2112_01508_gb300.slabs import EmulatedSlabs
+
+    def make_region(m):
+        return ShortRange(max(m, 1), w.x_s, w.x_r, w.G_m, softening="bspline", eps=w.eps, n_sub=1, device=dev)
+
+    def region_kernel_ms(em, calls=5):
+        em.forces(32)  # the first call after a change of decomposition sorts into it
+        ts = []
+        for _ in range(calls):
+            em.forces(32)
+            ts.append(sum(rk.stats().force_kernel_ms for rk in em.ranks))
+        return statistics.mean(ts)
+    regions = {"regions": 4, "force_calls": 64, "interval": 16, "kernel": "k_force_packed<bspline> per region "
+               "(receivers: the region's particles; suppliers: region + one-column halo)"}
+    em = EmulatedSlabs(pos_s, make_region, 4, n_subs=[1, 1, 1, 1])
+    regions["bounds"] = em.bounds
+    rr = RegionRefiner(em.ranks, interval=16, max_sub=4)
+    for _ in range(64):
+        rr.before_sort()
+        em.forces(32)
+        rr.after_forces()
+    rr.before_sort()
+    regions["chosen_n_sub"] = [c[0] for c in rr.current]
+    regions["chosen_ms"] = region_kernel_ms(em)
+    regions["trials"] = [[{"n_sub": e[1][0], "kept": e[4]} for e in log.events] for log in rr.logs]
+    uni = {}
+    for ns in (1, 2, 3, 4):
+        for rk in em.ranks:
+            rk.set_subtiles(ns)
+        uni[str(ns)] = region_kernel_ms(em)
+    regions["uniform_ms"] = uni
+    em.close()
     del pos_s
 
     # end to end through the public API with host buffers: every step's positions and
@@ -727,6 +766,7 @@ def run_ours(args):
             "long_range_pm": long_range,
             "differentiable_leapfrog": differentiable,
             "subtile_refinement": refinement,
+            "subtile_refinement_per_region": regions,
             "rung_substeps": rung_substeps,
             "rung_cycle": rung_cycle,
             "large_workloads": large,
@@ -740,6 +780,97 @@ def run_ours(args):
             "clocks": clocks,
             "wall_s_timed": t_wall,
         }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_slabs(args):
+    """The sharded path: each rank owns a work-balanced slab of tile columns of the 128^3
+    set; per step it sorts its particles, exchanges emigrants and the one-column halo with
+    its two neighbours (NCCL send/recv into its own memory), sorts particles plus halo,
+    computes the FP32 forces of its own particles and applies rungs, kick and drift.
+    Strong scaling: the whole set is fixed, value = pairs over all ranks / slowest rank."""
+    import torch
+
+    import synth
+    from paper_2112_01508_gb300 import ShortRange
+    from paper_2112_01508_gb300.slabs import DistTransport, SlabExchange, SlabRank, initial_split
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    w = synth.workload(args.workload)
+    n = w.n
+    eta, n_rung = 0.025, 8
+    pos = torch.from_numpy(synth.workload_positions(w)).to(dev)  # every rank draws the same set
+    mom = torch.zeros((3, n), dtype=torch.float64, device=dev)
+    rung = torch.zeros(n, dtype=torch.int8, device=dev)
+
+    def make(m):
+        return ShortRange(max(m, 1), w.x_s, w.x_r, w.G_m, softening="bspline", eps=w.eps, n_sub=w.n_sub,
+                          device=dev)
+    with make(n) as full:
+        # time step from the fake kick on the whole set, as in the single-GPU benchmark
+        full.sort(pos)
+        full.build_pairs()
+        a64 = full.forces(pos, 64)
+        amag = torch.linalg.vector_norm(a64, dim=0)
+        q99 = float(torch.quantile(amag[torch.randperm(n, device=dev, generator=torch.Generator(device=dev).manual_seed(0))[:1 << 20]].float(), 0.99))
+        del a64, amag
+        bounds, parts = initial_split(full, pos, [mom, rung], world)
+        n_t = full.stats_geometry()[0]
+    del pos, mom, rung
+    dt = 64.0 * (2.0 * eta * w.eps / max(q99, 1e-30)) ** 0.5
+    kick_factor = [dt / 2 ** l for l in range(n_rung)]
+    ex = SlabExchange(n_t, bounds, rank, world)
+    rk = SlabRank(make, ex)
+    tr = DistTransport()
+    own = parts[rank]
+    stream = torch.cuda.current_stream(dev)
+
+    def step(own):
+        col = rk.sort_own(own)
+        out = ex.prepare(own, col)
+        fl, fr = tr.swap(ex, out)
+        own, halo = ex.finish(out, fl, fr)
+        acc, pairs = rk.forces(own[0], halo, 32)
+        rk.kick_drift(own, acc, dt, eta, w.eps, kick_factor, dt / 2 ** (n_rung - 1))
+        return own, pairs, halo.shape[1]
+
+    for _ in range(args.warmup):
+        own, _, _ = step(own)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms, prs, halos, owns = [], [], [], []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        own, pairs, nh = step(own)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        prs.append(pairs)
+        halos.append(nh)
+        owns.append(own[0].shape[1])
+    barrier(world)
+    total_ms = max_over_ranks(sum(ms), world)
+    total_pairs = sum_over_ranks(float(sum(prs)), world)
+    rk.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": total_pairs / (total_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{w.name}: {w.description}", "n": n, "n_sub": w.n_sub,
+                           "softening": "bspline", "parallelism": f"slabs x{world} (tile columns along x, "
+                                                                  "one-column halo by NCCL send/recv)",
+                           "slab_bounds": bounds,
+                           "step": "sort own, exchange emigrants + halo, sort own + halo, FP32 forces of own "
+                                   "particles (one-sided), rungs+kick+drift"},
+                "rank0": {"own_particles": statistics.mean(owns), "halo_particles": statistics.mean(halos),
+                          "ms_per_step": statistics.mean(ms)}}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -805,6 +936,26 @@ def run_only(args):
         print(json.dumps(res))
         sr.close()
         return
+    if args.only == "kick":
+        # Eq. rung + kick + drift in one pass (p3m_sr_kick_drift) on the 128^3 state
+        mom = torch.zeros((3, w.n), dtype=torch.float64, device=dev)
+        rung = torch.zeros(w.n, dtype=torch.int8, device=dev)
+        sr.forces(pos, 32, acc32)
+        stream = torch.cuda.current_stream(dev)
+        dt = 1e-4
+        kf = [dt / 2 ** l for l in range(8)]
+        for k in range(args.warmup + args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sr.kick_drift(pos, mom, acc32, rung, dt, 0.025, w.eps, kf, dt / 128)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        print(json.dumps({"only": args.only, "workload": w.name, "kernel_ms": times}))
+        sr.close()
+        return
     if args.only == "forces32_gather":
         sr.set_symmetric(False)
     for k in range(args.warmup + args.steps):
@@ -859,6 +1010,8 @@ def main():
         run_reference(args)
     elif args.only:
         run_only(args)
+    elif args.mode == "slabs":
+        run_slabs(args)
     else:
         run_ours(args)
 

@@ -121,6 +121,29 @@ p3m_status p3m_sr_sync(p3m_sr_ctx* ctx);
 p3m_status p3m_sr_stats(p3m_sr_ctx* ctx, p3m_sr_stats_t* out);
 
 /*
+ * Change the number of particles of the following calls, for a domain whose
+ * particle count changes (Section 2.1.2, "Parallelisation": particles migrate
+ * between the domains of neighbouring processes as they move).
+ *   n  0 <= n <= the n given to p3m_sr_create (the context's capacity: no
+ *      memory is allocated or freed); larger values return P3M_ERR_INVALID.
+ * Every particle array of the following calls has n rows per component (a
+ * 3 x n SoA vector is x[0..n), y[0..n), z[0..n)).  The sort state is dropped:
+ * the next force, build_pairs or vjp call needs a p3m_sr_sort first.
+ */
+p3m_status p3m_sr_set_count(p3m_sr_ctx* ctx, int64_t n);
+
+/*
+ * Tile ranges of the last p3m_sr_sort (Section 2.1.3, "Tiles": the particles
+ * are stored tile by tile).  offsets_out: DEVICE array of n_t^3 + 1 int32;
+ * offsets_out[T] is the sorted index of the first particle of tile
+ * T = (t_x n_t + t_y) n_t + t_z and offsets_out[n_t^3] = n, so the particles of
+ * the slab of tile columns [c0, c1) along x are the sorted indices
+ * [offsets_out[c0 n_t^2], offsets_out[c1 n_t^2]).  Enqueued on the context's
+ * stream.  P3M_ERR_STATE before any sort (or after set_count / set_subtiles).
+ */
+p3m_status p3m_sr_tile_offsets(p3m_sr_ctx* ctx, int32_t* offsets_out);
+
+/*
  * Change the subtile decomposition (Section 2.1.3, "Subtiles": the number of
  * subtiles per tile is free, and the paper refines it while the simulation
  * runs by timing a force computation with one more subdivision).

@@ -7,7 +7,8 @@ rungs, kick, drift, adjoint; C ABI in ``include/p3m_sr.h``) and
 package holds their ctypes binding (``_native``), torch-facing wrappers
 (``ShortRange``, ``LongRange``), the differentiable force / leapfrog built on the
 forward and adjoint kernels (``autograd``), the rung-based leapfrog
-(``integrate``) and the timed subtile refinement (``refine``).
+(``integrate``), the timed subtile refinement (``refine``) and the slab
+decomposition over ranks with its halo exchange (``slabs``).
 """
 from .buildlib import build  # noqa: F401
 from .longrange import LongRange, PMStats  # noqa: F401

@@ -35,6 +35,7 @@ EXPORTS = (
     "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
     "p3m_sr_permute", "p3m_sr_unpermute", "p3m_sr_forces_noalloc", "p3m_sr_forces_tabulated",
     "p3m_sr_rung_kick", "p3m_sr_set_subtiles", "p3m_sr_set_symmetric", "p3m_sr_kick_drift",
+    "p3m_sr_set_count", "p3m_sr_tile_offsets",
 )
 
 
@@ -132,6 +133,10 @@ def load() -> ctypes.CDLL:
         L.p3m_sr_set_subtiles.restype = i
         L.p3m_sr_set_symmetric.argtypes = [p, i]
         L.p3m_sr_set_symmetric.restype = i
+        L.p3m_sr_set_count.argtypes = [p, ctypes.c_int64]
+        L.p3m_sr_set_count.restype = i
+        L.p3m_sr_tile_offsets.argtypes = [p, p]
+        L.p3m_sr_tile_offsets.restype = i
         _lib = L
         return L
 
@@ -347,3 +352,11 @@ def p3m_pm_assign(ctx, pos_ptr: int, rho_ptr: int) -> int:
 
 def p3m_pm_potential(ctx, phi_ptr: int) -> int:
     return load_pm().p3m_pm_potential(ctx, ctypes.c_void_p(phi_ptr))
+
+
+def p3m_sr_set_count(ctx, n) -> int:
+    return load().p3m_sr_set_count(ctx, int(n))
+
+
+def p3m_sr_tile_offsets(ctx, out_ptr) -> int:
+    return load().p3m_sr_tile_offsets(ctx, ctypes.c_void_p(out_ptr))

@@ -12,7 +12,8 @@ struct p3m_sr_ctx {
   int num_sms = 0;
   p3m::Geometry geo{};
   p3m::ForceConsts fc{};
-  int64_t n = 0;
+  int64_t n = 0;                      // particles of the following calls (p3m_sr_set_count)
+  int64_t cap = 0;                    // particles the scratch was allocated for (p3m_sr_create)
   int64_t n_tiles = 0;
 
   // ---- sort scratch ----

@@ -1771,11 +1771,11 @@ extern "C" p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precisi
     return st;
   if (n == 0) return P3M_OK;
   if (precision == 32 && !ctx->abar4) {
-    if ((st = cuda_check(ctx, cudaMalloc((void**)&ctx->abar4, sizeof(float4) * n), "cudaMalloc(abar4)")) != P3M_OK)
+    if ((st = cuda_check(ctx, cudaMalloc((void**)&ctx->abar4, sizeof(float4) * ctx->cap), "cudaMalloc(abar4)")) != P3M_OK)
       return st;
   }
   if (precision == 64 && !ctx->abar_d) {
-    if ((st = cuda_check(ctx, cudaMalloc((void**)&ctx->abar_d, sizeof(double) * 3 * n), "cudaMalloc(abar_d)")) != P3M_OK)
+    if ((st = cuda_check(ctx, cudaMalloc((void**)&ctx->abar_d, sizeof(double) * 3 * ctx->cap), "cudaMalloc(abar_d)")) != P3M_OK)
       return st;
   }
   if ((st = ensure_all_chunks(ctx)) != P3M_OK) return st;

@@ -239,7 +239,7 @@ static void setup_radix(p3m_sr_ctx* ctx) {
 
 // longest array the exclusive scan is applied to
 static int64_t scan_length(const p3m_sr_ctx* ctx) {
-  return std::max<int64_t>(std::max<int64_t>(ctx->geo.S + 1, ctx->n + 1),
+  return std::max<int64_t>(std::max<int64_t>(ctx->geo.S + 1, ctx->cap + 1),
                            std::max<int64_t>(ctx->hist_ints, ctx->n_tiles + 1));
 }
 
@@ -269,6 +269,7 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
   }
   ctx->prm = *params;
   ctx->n = params->n;
+  ctx->cap = params->n;
   ctx->stream = (cudaStream_t)cuda_stream;
   setup_geometry(ctx);
   setup_force_consts(ctx);
@@ -343,6 +344,20 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
 fail_alloc:
   p3m_sr_destroy(ctx);
   return st;
+}
+
+extern "C" p3m_status p3m_sr_set_count(p3m_sr_ctx* ctx, int64_t n) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (n < 0 || n > ctx->cap)
+    return fail(ctx, P3M_ERR_INVALID, "set_count: n must be in [0, the count given to p3m_sr_create]");
+  ctx->n = n;
+  ctx->prm.n = n;
+  ctx->sorted = false;
+  ctx->sorted_pos = nullptr;
+  ctx->pairs_built = false;
+  ctx->all_chunks_built = false;
+  ctx->perm = nullptr;
+  return P3M_OK;
 }
 
 extern "C" p3m_status p3m_sr_set_symmetric(p3m_sr_ctx* ctx, int enable) {

@@ -285,6 +285,22 @@ extern "C" p3m_status p3m_sr_sort(p3m_sr_ctx* ctx, double* pos, void* const* car
   return cuda_check(ctx, cudaMemsetAsync(ctx->drift_slots, 0, sizeof(float) * kMaxDrifts, s), "memset");
 }
 
+// out[T] = first sorted index of tile T (T = (t_x n_t + t_y) n_t + t_z), out[n_tiles] = n.
+__global__ void k_tile_offsets(const int* __restrict__ offsets, int64_t n_tiles, int nsub3, int* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= n_tiles) out[t] = offsets[t * nsub3];
+}
+
+extern "C" p3m_status p3m_sr_tile_offsets(p3m_sr_ctx* ctx, int32_t* offsets_out) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (!offsets_out) return fail(ctx, P3M_ERR_INVALID, "tile_offsets: null output");
+  if (!ctx->sorted) return fail(ctx, P3M_ERR_STATE, "tile_offsets: call p3m_sr_sort first");
+  const int64_t nt = ctx->n_tiles;
+  k_tile_offsets<<<blocks_for(nt + 1, 256), 256, 0, ctx->stream>>>(ctx->offsets, nt, ctx->geo.nsub3, offsets_out);
+  ++ctx->launches;
+  return cuda_check(ctx, cudaGetLastError(), "tile offsets kernel");
+}
+
 static p3m_status permute_rows(p3m_sr_ctx* ctx, const void* src, void* dst, int elem_bytes, int rows, int to_sorted,
                                const char* name) {
   if (!ctx) return P3M_ERR_INVALID;

@@ -1,13 +1,17 @@
-"""Temporal subtile refinement (Section 2.1.3, "Subtiles"; Section 4, subtile
-refinement figure).
+"""Subtile refinement, temporal and per region (Section 2.1.3, "Subtiles";
+Section 4, subtile refinement figure).
 
 The paper lets each process check, every 16th time step, whether one more
 subdivision of its tiles pays: it applies the refined subtiling for one
 short-range computation, compares the measured time with its record for the
-current subtiling, and keeps the refinement only if it was faster.  This
-single-GPU library has one domain, so one decomposition covers the whole box;
-the tiles are cubes, so all three dimensions are refined in lockstep (the
-"as cubic as possible" rule).
+current subtiling, and keeps the refinement only if it was faster.  Each
+process decides for its own domain, so the decomposition adapts in space as
+well as in time.  ``SubtileRefiner`` applies the rule to one context (one
+decomposition for the whole box); ``RegionRefiner`` applies it to every slab
+of a slab decomposition (``slabs.SlabRank``: a rank's domain, or a region of one
+GPU's box emulated as one), each slab keeping its own subtiling.  The tiles are
+cubes, so all three dimensions are refined in lockstep (the "as cubic as
+possible" rule).
 
 Because the receivers change from substep to substep under the rung scheme,
 the record and the trial are compared as device time per interacting pair
@@ -76,3 +80,29 @@ class SubtileRefiner:
     def _time_per_pair(self) -> float:
         st = self.sr.stats()
         return st.force_kernel_ms / max(st.pairs_last, 1)
+
+
+class RegionRefiner:
+    """Per-region subtile refinement: one ``SubtileRefiner`` per slab (anything with
+    ``n_sub``, ``set_subtiles`` and ``stats``, such as ``slabs.SlabRank``), each deciding
+    from the kernel time per pair of its own slab.  Call ``before_sort()`` before the
+    slabs' force contexts sort and ``after_forces()`` after every slab's force call."""
+
+    def __init__(self, slabs, interval: int = 16, max_sub: int = 8):
+        self.refiners = [SubtileRefiner(s, interval, max_sub) for s in slabs]
+
+    def before_sort(self):
+        for r in self.refiners:
+            r.before_sort()
+
+    def after_forces(self):
+        for r in self.refiners:
+            r.after_forces()
+
+    @property
+    def current(self) -> list:
+        return [r.current for r in self.refiners]
+
+    @property
+    def logs(self) -> list:
+        return [r.log for r in self.refiners]

@@ -107,6 +107,31 @@ class ShortRange:
         self._raise(nat.p3m_sr_set_symmetric(self._ctx, bool(enable)))
         self.symmetric = bool(enable)
 
+    def set_count(self, n: int):
+        """Particles of the following calls, at most the count given at creation
+        (p3m_sr_set_count; no allocation).  Sort again before the next force call."""
+        self._raise(nat.p3m_sr_set_count(self._ctx, int(n)))
+        self.n = int(n)
+
+    @property
+    def capacity(self) -> int:
+        return int(self.params.n)
+
+    def tile_offsets(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Sorted index of the first particle of every tile of the last sort, and n at the
+        end (p3m_sr_tile_offsets): a device tensor of n_t^3 + 1 int32."""
+        n_t = self.stats_geometry()[0]
+        if out is None:
+            out = torch.empty(n_t ** 3 + 1, dtype=torch.int32, device=self.device)
+        _check(out, "out", torch.int32, (n_t ** 3 + 1,), self.device)
+        self._raise(nat.p3m_sr_tile_offsets(self._ctx, out.data_ptr()))
+        return out
+
+    def stats_geometry(self):
+        """(n_t, n_sub): tiles per dimension and subtiles per tile, from the parameters."""
+        import math
+        return int(math.floor(self.params.box / self.params.x_r)), self.n_sub
+
     def set_subtiles(self, n_sub):
         """Change the subtiles per tile (p3m_sr_set_subtiles); sort again before the next force call."""
         ns = (n_sub,) * 3 if isinstance(n_sub, int) else tuple(int(v) for v in n_sub)
