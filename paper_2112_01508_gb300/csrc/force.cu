@@ -123,8 +123,47 @@ __device__ __forceinline__ void segment_range(const int* __restrict__ offsets, c
   a1 = tile_start(offsets, act_scan, nsub3, t1);
 }
 
+// Estimated cost of a chunk of segment `seg`: the particles within one tile of each
+// tile of the segment (summed over its tiles, 3 x 3 x 3 tiles each, periodic).  A
+// chunk's work is its surviving suppliers, which this count follows; it orders the
+// chunks so that the expensive ones start first (longest-processing-time-first).
+__device__ __forceinline__ unsigned long long segment_cost(const int* __restrict__ offsets, int nsub3, int n_t,
+                                                           int64_t seg) {
+  const int nseg = (n_t + kChunkSpan - 1) / kChunkSpan;
+  const int64_t row = seg / nseg;
+  const int k = (int)(seg - row * nseg);
+  const int tx = (int)(row / n_t), ty = (int)(row - (int64_t)tx * n_t);
+  const int tz0 = k * kChunkSpan, tz1 = min(n_t, tz0 + kChunkSpan);
+  unsigned long long est = 0;
+  for (int dx = -1; dx <= 1; ++dx) {
+    const int x = (tx + dx + n_t) % n_t;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int y = (ty + dy + n_t) % n_t;
+      const int64_t base = ((int64_t)x * n_t + y) * n_t;
+      for (int z = tz0 - 1; z <= tz1; ++z) {
+        // weight: the segment tiles within one tile of z along the row
+        const int w = min(z + 1, tz1 - 1) - max(z - 1, tz0) + 1;
+        if (w <= 0) continue;
+        const int zz = (z + n_t) % n_t;
+        const int64_t T = base + zz;
+        est += (unsigned long long)w * (unsigned long long)(offsets[(T + 1) * nsub3] - offsets[T * nsub3]);
+      }
+    }
+  }
+  return est;
+}
+
+__device__ __forceinline__ int cost_bucket(unsigned long long v) {
+  if (v < 4) return (int)v;
+  const int e = 63 - __clzll((long long)v);
+  return min(kCostBuckets - 1, 4 * e + (int)((v >> (e - 2)) & 3) - 4);
+}
+
+// seg_bucket / bucket_count (nullable): the cost bucket of each segment and the
+// number of chunks per bucket (bucket_count zeroed before the launch).
 __global__ void k_row_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int n_t, int nsub3,
-                             int* __restrict__ seg_chunks) {
+                             int* __restrict__ seg_chunks, unsigned char* __restrict__ seg_bucket,
+                             int* __restrict__ bucket_count) {
   const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nsegs = (int64_t)n_t * n_t * ((n_t + kChunkSpan - 1) / kChunkSpan);
   if (seg > nsegs) return;
@@ -134,12 +173,35 @@ __global__ void k_row_chunks(const int* __restrict__ offsets, const int* __restr
   }
   int a0, a1;
   segment_range(offsets, act_scan, nsub3, n_t, seg, a0, a1);
-  seg_chunks[seg] = (a1 - a0 + kChunk - 1) / kChunk;
+  const int nc = (a1 - a0 + kChunk - 1) / kChunk;
+  seg_chunks[seg] = nc;
+  if (seg_bucket && nc > 0) {
+    const int b = cost_bucket(segment_cost(offsets, nsub3, n_t, seg));
+    seg_bucket[seg] = (unsigned char)b;
+    atomicAdd(&bucket_count[b], nc);
+  }
 }
 
+// Chunks per cost bucket -> first position of each bucket in the processing order,
+// the most expensive bucket first (one block of kCostBuckets threads).
+__global__ void k_bucket_offsets(int* __restrict__ bucket) {
+  __shared__ int c[kCostBuckets];
+  const int t = threadIdx.x;
+  c[t] = bucket[t];
+  __syncthreads();
+  int s = 0;
+  for (int u = t + 1; u < kCostBuckets; ++u) s += c[u];
+  bucket[t] = s;
+}
+
+// order (nullable): the chunk indices in decreasing estimated cost (bucket cursors from
+// k_bucket_offsets; the order within a bucket depends on the order of execution, the
+// results do not).
 __global__ void k_write_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int n_t, int nsub3,
                                const int* __restrict__ seg_chunks, Chunk* __restrict__ chunks,
-                               int* __restrict__ n_chunks_out, int* __restrict__ n_active_out, int64_t n) {
+                               int* __restrict__ n_chunks_out, int* __restrict__ n_active_out, int64_t n,
+                               const unsigned char* __restrict__ seg_bucket, int* __restrict__ bucket_cursor,
+                               int* __restrict__ order) {
   const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nsegs = (int64_t)n_t * n_t * ((n_t + kChunkSpan - 1) / kChunkSpan);
   if (seg == 0) {
@@ -149,10 +211,17 @@ __global__ void k_write_chunks(const int* __restrict__ offsets, const int* __res
   if (seg >= nsegs) return;
   int a0, a1;
   segment_range(offsets, act_scan, nsub3, n_t, seg, a0, a1);
-  Chunk* out = chunks + seg_chunks[seg];
+  const int first = seg_chunks[seg];
+  Chunk* out = chunks + first;
+  int nc = 0;
   for (int k = 0; a0 + k * kChunk < a1; ++k) {
     const int s0 = a0 + k * kChunk;
     out[k] = Chunk{s0, min(kChunk, a1 - s0)};
+    ++nc;
+  }
+  if (order && nc > 0) {
+    const int p = atomicAdd(&bucket_cursor[seg_bucket[seg]], nc);
+    for (int k = 0; k < nc; ++k) order[p + k] = first + k;
   }
 }
 
@@ -188,6 +257,8 @@ struct TraversalArgs {
   const int* offsets;         // S + 1 subtile offsets
   const int* cell;            // sorted subtile ids
   const Chunk* chunks;
+  const int* order;           // processing order of the chunks (decreasing estimated cost), or nullptr
+  float4* part_acc;           // per (work item, lane) partial sums when chunks are split (kPartItems x 32), or nullptr
   const float* drift_slots;   // displacement bounds of the drifts since the sort (device)
   int n_drift;                // how many of them
   int* err;                   // device error bits (kErrDrift), or nullptr
@@ -424,16 +495,19 @@ __device__ __forceinline__ void append_round(WarpList& L, int lane, bool take, i
 // (32 candidates per round, one per lane), keep those whose box gap to the
 // receivers' bounding box is below x_r and that hold particles, and append their
 // particle ranges to the warp's list; `proc(nlist, total)` consumes a full list.
+// With nparts > 1 only every nparts-th candidate subtile, starting at `part`, is
+// enumerated: the parts of a chunk split its suppliers between work items.
 template <class Real, class Proc>
 __device__ __forceinline__ void enumerate_suppliers(const TraversalArgs& a, const Reach& rc, const ChunkFrame<Real>& F,
-                                                    WarpList& L, int lane, Proc&& proc) {
+                                                    WarpList& L, int lane, int part, int nparts, Proc&& proc) {
   const unsigned full = 0xffffffffu;
-  const int ncand = F.ext[0] * F.ext[1] * F.ext[2];
+  const int ncand_all = F.ext[0] * F.ext[1] * F.ext[2];
+  const int ncand = (ncand_all - part + nparts - 1) / nparts;  // candidates of this part
   int nlist = 0, total = 0;
   for (int cb = 0; cb < ncand; cb += kWarp) {
     int start, cnt;
     unsigned dpk;
-    const bool take = candidate_range<Real>(a, rc, F, cb + lane, ncand, 0, start, cnt, dpk);
+    const bool take = candidate_range<Real>(a, rc, F, (cb + lane) * nparts + part, ncand_all, 0, start, cnt, dpk);
     const unsigned tm = __ballot_sync(full, take);
     if (tm == 0) continue;
     if (nlist + __popc(tm) > kListCap) {
@@ -619,6 +693,30 @@ __device__ __forceinline__ int next_chunk(const TraversalArgs& a, int lane) {
   return __shfl_sync(0xffffffffu, c, 0);
 }
 
+// Chunk processing order.  The chunk list is in the sorted (spatial) order, which
+// keeps neighbouring chunks, and the suppliers they share, together in L2.  With
+// few chunks (split into parts, below) the cost-ordered list is used instead so
+// that the most expensive chunks start first.  P3M_LPT: 0 never, 1 with split
+// chunks only, 2 always (tuning builds).
+#ifndef P3M_LPT
+#define P3M_LPT 1
+#endif
+
+// The c-th chunk to process (c < n_chunks).
+__device__ __forceinline__ Chunk chunk_at(const TraversalArgs& a, int c, bool by_cost = P3M_LPT == 2) {
+  return a.chunks[(a.order && by_cost) ? a.order[c] : c];
+}
+
+// Work items per chunk of the one-sided kernel: with few chunks (sparse receivers,
+// the deepest rungs) each chunk's candidate subtiles are split between up to
+// kMaxParts work items so that every resident warp has work; their partial sums
+// are added in a fixed order by k_parts_finish.
+__host__ __device__ __forceinline__ int parts_for(int n_chunks) {
+  if (n_chunks <= 0) return 1;
+  const int k = kPartItems / n_chunks;
+  return k < 1 ? 1 : (k > kMaxParts ? kMaxParts : k);
+}
+
 template <class Real, bool VJP, int SOFT>
 __global__ void __launch_bounds__(kForceThreads) k_traverse(TraversalArgs a) {
   __shared__ WarpList lists[kForceWarps];
@@ -632,7 +730,7 @@ __global__ void __launch_bounds__(kForceThreads) k_traverse(TraversalArgs a) {
     const int c = next_chunk(a, lane);
     if (c >= n_chunks) break;
     ChunkFrame<Real> F;
-    load_chunk<Real>(a, rc, a.chunks[c], lane, F);
+    load_chunk<Real>(a, rc, chunk_at(a, c), lane, F);
     Vec3<Real> abar_i = {Real(0), Real(0), Real(0)};
     if (VJP && F.valid) {
       if constexpr (sizeof(Real) == 4) {
@@ -644,7 +742,7 @@ __global__ void __launch_bounds__(kForceThreads) k_traverse(TraversalArgs a) {
     }
     Vec3<Real> acc = {Real(0), Real(0), Real(0)};
     int hits = 0;
-    enumerate_suppliers<Real>(a, rc, F, L, lane, [&](int nlist, int total) {
+    enumerate_suppliers<Real>(a, rc, F, L, lane, 0, 1, [&](int nlist, int total) {
       process_list<Real, VJP, SOFT>(a, L, nlist, total, lane, F, abar_i, acc, hits);
     });
     store_result<Real>(a, F, acc);
@@ -700,19 +798,22 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
   const int lane = threadIdx.x & 31;
   PackedSmem& S = smem[threadIdx.x >> 5];
   const int n_chunks = *a.n_chunks;
+  const int nparts = a.part_acc ? parts_for(n_chunks) : 1;
+  const int n_items = n_chunks * nparts;
   const Reach rc = make_reach(a);
   const float xr2 = a.f.xr2_f;
   const float xr2s = xr2 * kCutScale;
   unsigned long long pair_total = 0;
   for (;;) {
-    const int c = next_chunk(a, lane);
-    if (c >= n_chunks) break;
+    const int w = next_chunk(a, lane);
+    if (w >= n_items) break;
+    const int c = w / nparts, part = w - c * nparts;
     ChunkFrame<float> F;
-    load_chunk<float>(a, rc, a.chunks[c], lane, F);
+    load_chunk<float>(a, rc, chunk_at(a, c, P3M_LPT == 2 || (P3M_LPT == 1 && nparts > 1)), lane, F);
     const f2 px = pk(F.pi.x, F.pi.x), py = pk(F.pi.y, F.pi.y), pz = pk(F.pi.z, F.pi.z);
     f2 ax = pk(0.f, 0.f), ay = pk(0.f, 0.f), az = pk(0.f, 0.f);
     f2 hitsf = pk(0.f, 0.f);  // interacting pairs of this lane (exact integers in FP32)
-    enumerate_suppliers<float>(a, rc, F, S.L, lane, [&](int nlist, int total) {
+    enumerate_suppliers<float>(a, rc, F, S.L, lane, part, nparts, [&](int nlist, int total) {
       float* sxy = (float*)S.sxy;
       float* sz = (float*)S.sz;
       const WarpList& L = S.L;
@@ -843,12 +944,44 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
     acc.y = l + h;
     upk(az, l, h);
     acc.z = l + h;
-    store_result<float>(a, F, acc);
+    if (nparts == 1) store_result<float>(a, F, acc);
+    else a.part_acc[(int64_t)w * kWarp + lane] = make_float4(acc.x, acc.y, acc.z, 0.f);
     upk(hitsf, l, h);
-    const int hits = F.valid ? (int)(l + h) - 1 : 0;  // the receiver met itself once (r = 0)
-    pair_total += (unsigned long long)__reduce_add_sync(full, (unsigned)hits);
+    // the receiver met itself once (r = 0), in the part that holds its own subtile; every
+    // part counts its hits, and part 0 takes off one per receiver
+    const int hits = F.valid ? (int)(l + h) - (part == 0 ? 1 : 0) : 0;
+    // signed: a part-0 lane whose own subtile lies in another part counts -1; the sum
+    // over a chunk's parts is exact, and the 64-bit total wraps back
+    pair_total += (unsigned long long)(long long)__reduce_add_sync(full, hits);
   }
   if (lane == 0 && pair_total) atomicAdd(a.pairs, pair_total);
+}
+
+// acc = -G m (sum of the parts of each chunk, in part order), when k_force_packed
+// split its chunks (nothing to do otherwise).  One warp per chunk position.
+__global__ void k_parts_finish(TraversalArgs a) {
+  const int n_chunks = *a.n_chunks;
+  const int nparts = parts_for(n_chunks);
+  if (nparts == 1) return;
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const float s = -(float)a.f.G_m;
+  float* o = (float*)a.out;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += nw) {
+    const Chunk ch = chunk_at(a, c, P3M_LPT >= 1);
+    if (lane >= ch.count) continue;
+    const int pidx = a.active_idx ? a.active_idx[ch.start + lane] : ch.start + lane;
+    float x = 0.f, y = 0.f, z = 0.f;
+    for (int k = 0; k < nparts; ++k) {
+      const float4 v = a.part_acc[((int64_t)c * nparts + k) * kWarp + lane];
+      x += v.x;
+      y += v.y;
+      z += v.z;
+    }
+    o[pidx] = s * x;
+    o[a.n + pidx] = s * y;
+    o[2 * a.n + pidx] = s * z;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -932,7 +1065,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
   for (;;) {
     const int c = next_chunk(a, lane);
     if (c >= n_chunks) break;
-    const Chunk ch = a.chunks[c];
+    const Chunk ch = chunk_at(a, c);
     ChunkFrame<float> F;
     load_chunk<float>(a, rc, ch, lane, F);
     const int i_self = F.valid ? F.pidx : 0x7fffffff;  // the mask j > i is false on empty lanes
@@ -1335,14 +1468,14 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_vjp_packed(Trav
     const int c = next_chunk(a, lane);
     if (c >= n_chunks) break;
     ChunkFrame<float> F;
-    load_chunk<float>(a, rc, a.chunks[c], lane, F);
+    load_chunk<float>(a, rc, chunk_at(a, c), lane, F);
     const f2 px = pk(F.pi.x, F.pi.x), py = pk(F.pi.y, F.pi.y), pz = pk(F.pi.z, F.pi.z);
     float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
     if (F.valid) ab = a.abar4[F.pidx];
     const f2 vix = pk(ab.x, ab.x), viy = pk(ab.y, ab.y), viz = pk(ab.z, ab.z);
     f2 gx = pk(0.f, 0.f), gy = pk(0.f, 0.f), gz = pk(0.f, 0.f);
     int hits = 0;
-    enumerate_suppliers<float>(a, rc, F, S.L, lane, [&](int nlist, int total) {
+    enumerate_suppliers<float>(a, rc, F, S.L, lane, 0, 1, [&](int nlist, int total) {
       float* sxy = (float*)S.sxy;
       float* sz = (float*)S.sz;
       float* vxy = (float*)S.vxy;
@@ -1487,16 +1620,22 @@ static cudaError_t launch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
   }
   unsigned grid = (unsigned)(ctx->num_sms * blocks_per_sm);
   const int slot = VJP ? 1 : 0;
+  TraversalArgs ap = a;
+  if (packed && !VJP) ap.part_acc = ctx->part_acc;  // sparse receivers: chunks split into parts
   cudaEventRecord(ctx->kt_ev[2 * slot], ctx->stream);
   if (packed && !VJP)
-    k_force_packed<SOFT><<<grid, kPThreads, 0, ctx->stream>>>(a);
+    k_force_packed<SOFT><<<grid, kPThreads, 0, ctx->stream>>>(ap);
   else if (packed)
-    k_vjp_packed<SOFT><<<grid, kPThreads, 0, ctx->stream>>>(a);
+    k_vjp_packed<SOFT><<<grid, kPThreads, 0, ctx->stream>>>(ap);
   else
-    k_traverse<Real, VJP, SOFT><<<grid, kForceThreads, 0, ctx->stream>>>(a);
+    k_traverse<Real, VJP, SOFT><<<grid, kForceThreads, 0, ctx->stream>>>(ap);
   ++ctx->launches;
   cudaEventRecord(ctx->kt_ev[2 * slot + 1], ctx->stream);
   ctx->kt_pending[slot] = true;
+  if (packed && !VJP) {
+    k_parts_finish<<<(unsigned)(ctx->num_sms * 4), 256, 0, ctx->stream>>>(ap);
+    ++ctx->launches;
+  }
   return cudaGetLastError();
 }
 
@@ -1543,29 +1682,34 @@ static cudaError_t dispatch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
   }
 }
 
-static p3m_status build_chunks(p3m_sr_ctx* ctx, const int* act_scan, Chunk* chunks, int* n_chunks_dev,
+// Receiver chunks of the row segments, and their processing order by estimated cost.
+static p3m_status build_chunks(p3m_sr_ctx* ctx, const int* act_scan, Chunk* chunks, int* order, int* n_chunks_dev,
                                int* n_active_dev) {
   cudaStream_t s = ctx->stream;
   const int n_t = ctx->geo.n_t;
   const int64_t rows = (int64_t)n_t * n_t * ((n_t + kChunkSpan - 1) / kChunkSpan);  // segments
-  k_row_chunks<<<blocks_for(rows + 1, 128), 128, 0, s>>>(ctx->offsets, act_scan, n_t, ctx->geo.nsub3,
-                                                         ctx->tile_chunks);
-  ++ctx->launches;
-  p3m_status st = cuda_check(ctx, cudaGetLastError(), "row chunk kernel");
+  p3m_status st = cuda_check(ctx, cudaMemsetAsync(ctx->bucket_cursor, 0, sizeof(int) * kCostBuckets, s), "memset");
   if (st != P3M_OK) return st;
+  k_row_chunks<<<blocks_for(rows + 1, 128), 128, 0, s>>>(ctx->offsets, act_scan, n_t, ctx->geo.nsub3,
+                                                         ctx->tile_chunks, ctx->seg_bucket, ctx->bucket_cursor);
+  ++ctx->launches;
+  if ((st = cuda_check(ctx, cudaGetLastError(), "row chunk kernel")) != P3M_OK) return st;
   st = cuda_check(ctx, scan_exclusive_i32(ctx->tile_chunks, ctx->tile_chunks, rows + 1, ctx->scan_scratch, s,
                                           &ctx->launches), "chunk scan");
   if (st != P3M_OK) return st;
+  k_bucket_offsets<<<1, kCostBuckets, 0, s>>>(ctx->bucket_cursor);
+  ++ctx->launches;
+  if ((st = cuda_check(ctx, cudaGetLastError(), "bucket offsets kernel")) != P3M_OK) return st;
   k_write_chunks<<<blocks_for(rows, 128), 128, 0, s>>>(ctx->offsets, act_scan, n_t, ctx->geo.nsub3,
                                                         ctx->tile_chunks, chunks, n_chunks_dev, n_active_dev,
-                                                        ctx->n);
+                                                        ctx->n, ctx->seg_bucket, ctx->bucket_cursor, order);
   ++ctx->launches;
   return cuda_check(ctx, cudaGetLastError(), "write chunks kernel");
 }
 
 p3m_status ensure_all_chunks(p3m_sr_ctx* ctx) {
   if (ctx->all_chunks_built) return P3M_OK;
-  p3m_status st = build_chunks(ctx, nullptr, ctx->chunks_all, ctx->dev_small + 1, nullptr);
+  p3m_status st = build_chunks(ctx, nullptr, ctx->chunks_all, ctx->order_all, ctx->dev_small + 1, nullptr);
   if (st == P3M_OK) ctx->all_chunks_built = true;
   return st;
 }
@@ -1622,7 +1766,7 @@ extern "C" p3m_status p3m_sr_build_pairs(p3m_sr_ctx* ctx, const int8_t* rung, in
     }
     act_scan = ctx->act_scan;
   }
-  st = build_chunks(ctx, act_scan, ctx->chunks, ctx->dev_small + 0, ctx->dev_small + 2);
+  st = build_chunks(ctx, act_scan, ctx->chunks, ctx->order, ctx->dev_small + 0, ctx->dev_small + 2);
   if (st != P3M_OK) return st;
   ctx->pairs_built = true;
   return P3M_OK;
@@ -1647,6 +1791,7 @@ extern "C" p3m_status p3m_sr_forces(p3m_sr_ctx* ctx, const double* pos, int prec
   TraversalArgs a = base_args(ctx);
   a.pos = pos;
   a.chunks = ctx->chunks;
+  a.order = ctx->order;
   a.n_chunks = ctx->dev_small + 0;
   a.counter = ctx->dev_small + 3;
   a.active_idx = ctx->all_active ? nullptr : ctx->active_idx;
@@ -1725,11 +1870,13 @@ extern "C" p3m_status p3m_sr_forces_tabulated(p3m_sr_ctx* ctx, const double* pos
   TraversalArgs a = base_args(ctx);
   a.pos = pos;
   a.chunks = ctx->chunks;
+  a.order = ctx->order;
   a.n_chunks = ctx->dev_small + 0;
   a.counter = ctx->dev_small + 3;
   a.active_idx = ctx->all_active ? nullptr : ctx->active_idx;
   a.out = acc_out;
   a.table = ctx->table;
+  a.part_acc = ctx->part_acc;
   a.n_table = nt;
   a.table_scale = (float)(nt / (ctx->prm.x_r * ctx->prm.x_r));
   const size_t shm = sizeof(float) * nt;
@@ -1743,6 +1890,8 @@ extern "C" p3m_status p3m_sr_forces_tabulated(p3m_sr_ctx* ctx, const double* pos
     ++ctx->launches;
     cudaEventRecord(ctx->kt_ev[1], s);
     ctx->kt_pending[0] = true;
+    k_parts_finish<<<(unsigned)(ctx->num_sms * 4), 256, 0, s>>>(a);
+    ++ctx->launches;
   };
   switch (ctx->prm.softening) {
     case P3M_SOFT_NONE: launch(k_force_packed<P3M_SOFT_NONE, true>); break;
@@ -1792,6 +1941,7 @@ extern "C" p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precisi
   TraversalArgs a = base_args(ctx);
   a.pos = pos;
   a.chunks = ctx->chunks_all;
+  a.order = ctx->order_all;
   a.n_chunks = ctx->dev_small + 1;
   a.counter = ctx->dev_small + 4;
   a.active_idx = nullptr;
@@ -2006,11 +2156,12 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   // receiver chunks (all particles active)
   const int64_t nrows = (int64_t)g.n_t * g.n_t * ((g.n_t + kChunkSpan - 1) / kChunkSpan);  // segments
-  k_row_chunks<<<(unsigned)((nrows + 1 + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows);
+  k_row_chunks<<<(unsigned)((nrows + 1 + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows, nullptr,
+                                                                   nullptr);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   if (!ok(scan_exclusive_i32(rows, rows, nrows + 1, scan, s, &launches))) return P3M_ERR_CUDA;
   k_write_chunks<<<(unsigned)((nrows + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows, chunks,
-                                                                 small + 0, nullptr, n);
+                                                                 small + 0, nullptr, n, nullptr, nullptr, nullptr);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   // pair forces in the sorted order, then back to the caller's order
   static SeriesConsts series = make_series();
