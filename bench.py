@@ -293,11 +293,12 @@ def large_record(wname: str, dev, with_cpu: bool, steps: int = 2):
         mom = torch.zeros((3, n), dtype=torch.float32 if n > (1 << 28) else torch.float64, device=dev)
         kick_factor = [dt / 2 ** l for l in range(n_rung)]
         step_ms, step_pairs = [], []
+        scr = [torch.empty_like(p), torch.empty_like(mom), torch.empty_like(rung)]
         for k in range(1 + steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            sr.sort(p, carry=[mom, rung])
+            sr.sort(p, carry=[mom, rung], scratch=scr)
             sr.build_pairs()
             sr.forces(p, 32, a32)
             sr.kick_drift(p, mom, a32, rung, dt, eta, w.eps, kick_factor, dt / 2 ** (n_rung - 1))
@@ -310,7 +311,7 @@ def large_record(wname: str, dev, with_cpu: bool, steps: int = 2):
                             "value": sum(step_pairs) / (sum(step_ms) * 1e-3), "unit": UNIT,
                             "momenta": str(mom.dtype).replace("torch.", ""),
                             "step": "sort+carry, work list, FP32 forces, rungs+kick+drift"}
-        del p, a32, mom, rung
+        del p, a32, mom, rung, scr
     torch.cuda.empty_cache()
     if with_cpu:
         import oracle
@@ -369,7 +370,7 @@ def run_ours(args):
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        sr.sort(pos, carry=[mom, rung])
+        sr.sort(pos, carry=[mom, rung], scratch=scratch)  # out of place, storages swapped
         if ev is not None:
             ev[1].record(stream)
         sr.build_pairs()
@@ -381,6 +382,7 @@ def run_ours(args):
             ev[3].record(stream)
 
     stream = torch.cuda.current_stream(dev)
+    scratch = [torch.empty_like(pos), torch.empty_like(mom), torch.empty_like(rung)]
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -560,7 +562,7 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            sr.sort(pos, carry=[mom, rung])
+            sr.sort(pos, carry=[mom, rung], scratch=scratch)
             sr.build_pairs(None if lc == 0 else rung, lc)
             sr.forces(pos, 32, acc)
             sr.kick(mom, acc, [0.0] * n_rung, rung, lc)  # zero kick: timed, state unchanged
@@ -686,8 +688,10 @@ def run_ours(args):
             Q[i].copy_(mom_host, non_blocking=True)
             copied[i].record(copy_stream)
 
+    S = [[torch.empty_like(pos), torch.empty_like(mom), torch.empty_like(rung)] for _ in range(2)]
+
     def step_on(i):
-        sr.sort(P[i], carry=[Q[i], R[i]])
+        sr.sort(P[i], carry=[Q[i], R[i]], scratch=S[i])
         sr.build_pairs()
         sr.forces(P[i], 32, A[i])
         sr.kick_drift(P[i], Q[i], A[i], R[i], dt, eta, w.eps, kick_factor, drift_factor)
@@ -737,7 +741,7 @@ def run_ours(args):
                                "sample": f"{nrecv1} seeded receivers, {cp1} pairs, {secs1:.1f} s"}}
 
     sr.close()
-    del flush, P, Q, R, A, pos0, acc64
+    del flush, P, Q, R, A, S, scratch, pos0, acc64
     torch.cuda.empty_cache()
     large = {}
     if world == 1 and not args.no_large:

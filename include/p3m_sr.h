@@ -179,6 +179,22 @@ p3m_status p3m_sr_sort(p3m_sr_ctx* ctx, double* pos, void* const* carry, const i
                        int n_carry, int32_t* perm_out, int32_t* subtile_id_out);
 
 /*
+ * Out-of-place variant of p3m_sr_sort (same binning, same stable order): the
+ * sorted positions and carried arrays are written to separate output arrays in
+ * one pass and the inputs are left unchanged, which halves the memory traffic of
+ * the reordering (no copy back).  Callers alternate two sets of buffers.
+ *   pos_in, pos_out   3 x n float64 SoA, device, distinct (each position of pos_in
+ *                     finite and in [0, L), as for p3m_sr_sort).
+ *   carry_in, carry_out  n_carry (at most 8) pairs of distinct device arrays of n
+ *                     elements of carry_bytes[c] bytes (1..32).
+ *   perm_out, subtile_id_out  as for p3m_sr_sort.
+ * After the call the sort describes pos_out (drifting pos_out keeps it usable).
+ */
+p3m_status p3m_sr_sort_into(p3m_sr_ctx* ctx, const double* pos_in, double* pos_out, const void* const* carry_in,
+                            void* const* carry_out, const int* carry_bytes, int n_carry, int32_t* perm_out,
+                            int32_t* subtile_id_out);
+
+/*
  * Move per-particle data between the caller's order and the order of the last
  * p3m_sr_sort (the tile -> subtile walk order of Section 2.1.3), for data that
  * was not carried through the sort (for example to return accelerations in the

@@ -35,7 +35,7 @@ EXPORTS = (
     "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
     "p3m_sr_permute", "p3m_sr_unpermute", "p3m_sr_forces_noalloc", "p3m_sr_forces_tabulated",
     "p3m_sr_rung_kick", "p3m_sr_set_subtiles", "p3m_sr_set_symmetric", "p3m_sr_kick_drift",
-    "p3m_sr_set_count", "p3m_sr_tile_offsets",
+    "p3m_sr_set_count", "p3m_sr_tile_offsets", "p3m_sr_sort_into",
 )
 
 
@@ -133,6 +133,8 @@ def load() -> ctypes.CDLL:
         L.p3m_sr_set_subtiles.restype = i
         L.p3m_sr_set_symmetric.argtypes = [p, i]
         L.p3m_sr_set_symmetric.restype = i
+        L.p3m_sr_sort_into.argtypes = [p, p, p, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(i), i, p, p]
+        L.p3m_sr_sort_into.restype = i
         L.p3m_sr_set_count.argtypes = [p, ctypes.c_int64]
         L.p3m_sr_set_count.restype = i
         L.p3m_sr_tile_offsets.argtypes = [p, p]
@@ -360,3 +362,12 @@ def p3m_sr_set_count(ctx, n) -> int:
 
 def p3m_sr_tile_offsets(ctx, out_ptr) -> int:
     return load().p3m_sr_tile_offsets(ctx, ctypes.c_void_p(out_ptr))
+
+
+def p3m_sr_sort_into(ctx, pos_in, pos_out, carry_in, carry_out, carry_bytes, perm_ptr, ids_ptr) -> int:
+    k = len(carry_out)
+    ci = (ctypes.c_void_p * max(k, 1))(*[ctypes.c_void_p(x) for x in carry_in])
+    co = (ctypes.c_void_p * max(k, 1))(*[ctypes.c_void_p(x) for x in carry_out])
+    cb = (ctypes.c_int * max(k, 1))(*carry_bytes)
+    return load().p3m_sr_sort_into(ctx, ctypes.c_void_p(pos_in), ctypes.c_void_p(pos_out), ci, co, cb, k,
+                                   ctypes.c_void_p(perm_ptr or 0), ctypes.c_void_p(ids_ptr or 0))

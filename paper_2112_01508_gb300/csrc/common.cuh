@@ -104,7 +104,8 @@ __global__ void k_radix_hist(const int* __restrict__ keys, int64_t n, int shift,
                              int nblocks);
 __global__ void k_radix_scatter(const int* __restrict__ keys_in, const int* __restrict__ vals_in,
                                 int* __restrict__ keys_out, int* __restrict__ vals_out, int64_t n, int shift,
-                                int bits, const int* __restrict__ hist, int nblocks);
+                                int bits, const int* __restrict__ hist, int nblocks, int* __restrict__ hist_next,
+                                int shift_next, int bits_next);
 __global__ void k_gather_pos(const double* __restrict__ src, const int* __restrict__ perm, int64_t n,
                              double* __restrict__ dst);
 

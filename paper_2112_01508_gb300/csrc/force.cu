@@ -2144,7 +2144,7 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
     if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
     if (!ok(scan_exclusive_i32(hist, hist, (int64_t)nblocks << bits, scan, s, &launches))) return P3M_ERR_CUDA;
     k_radix_scatter<<<nblocks, kRadixThreadsPublic, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n,
-                                                            shift, bits, hist, nblocks);
+                                                            shift, bits, hist, nblocks, nullptr, 0, 0);
     if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
     cur ^= 1;
     shift += bits;

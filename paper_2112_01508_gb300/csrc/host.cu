@@ -297,7 +297,7 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
   P3M_ALLOC(ctx->vals[0], n);
   P3M_ALLOC(ctx->vals[1], n);
   P3M_ALLOC(ctx->offsets, S + 1);
-  P3M_ALLOC(ctx->hist, ctx->hist_ints);
+  P3M_ALLOC(ctx->hist, 2 * ctx->hist_ints);  // this radix pass's digit counts and the next pass's
   P3M_ALLOC(ctx->scan_scratch, ctx->scan_scratch_ints);
   {
     char* gt = nullptr;

@@ -56,7 +56,8 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
     rung = torch.zeros(sr.n, dtype=torch.int8, device=dev)
     state = torch.zeros(sr.n, dtype=torch.int8, device=dev)
     carried = [mom, rung, state, *carry]
-    sr.sort(pos, carry=carried)
+    scratch = [torch.empty_like(t) for t in (pos, *carried)]  # out-of-place sorts, storage swapped back
+    sr.sort(pos, carry=carried, scratch=scratch)
     sr.build_pairs()
     acc = sr.forces(pos, precision)
     acc_lr = None if long_range is None else torch.empty((3, sr.n), dtype=long_range.dtype, device=dev)
@@ -76,7 +77,7 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
             k += 1
             sr.drift(pos, mom, dt / sub)
             if k % resort_every == 0:
-                sr.sort(pos, carry=carried)
+                sr.sort(pos, carry=carried, scratch=scratch)
             lmin = substep_rung_min(k, n_rung)
             sr.build_pairs(None if lmin == 0 else rung, lmin)  # lmin 0: all receivers (each pair once in FP32)
             sr.forces(pos, precision, acc)

@@ -42,6 +42,15 @@ def _check(t: torch.Tensor, name: str, dtype=None, shape=None, device=None):
         raise ValueError(f"{name} must be on {device}, got {t.device}")
 
 
+def _swap_storage(a: torch.Tensor, b: torch.Tensor):
+    """Exchange the memory behind two tensors of one shape and dtype (no copy)."""
+    sa, sb = a.untyped_storage(), b.untyped_storage()
+    oa, ob = a.storage_offset(), b.storage_offset()
+    shape, sta, stb = a.shape, a.stride(), b.stride()
+    a.set_(sb, ob, shape, stb)
+    b.set_(sa, oa, shape, sta)
+
+
 class ShortRange:
     """Short-range P3M force context for ``n`` particles (see include/p3m_sr.h)."""
 
@@ -139,8 +148,20 @@ class ShortRange:
         self.n_sub = ns
 
     def sort(self, pos: torch.Tensor, carry=(), perm_out: torch.Tensor | None = None,
-             subtile_id_out: torch.Tensor | None = None):
-        """Sort in place into tile -> subtile walk order (p3m_sr_sort)."""
+             subtile_id_out: torch.Tensor | None = None, scratch=None):
+        """Sort into tile -> subtile walk order.  Without `scratch`: in place (p3m_sr_sort).
+        With `scratch`, a list of tensors like [pos, *carry]: out of place into the scratch
+        tensors (p3m_sr_sort_into, no copy back), after which each tensor and its scratch
+        exchange their storage, so pos and carry hold the sorted data as after an
+        in-place sort and the scratch tensors hold the old data."""
+        if scratch is not None:
+            arrays = [pos, *carry]
+            if len(scratch) != len(arrays):
+                raise ValueError("scratch must hold one tensor per array of [pos, *carry]")
+            self.sort_into(pos, scratch[0], carry, scratch[1:], perm_out, subtile_id_out)
+            for a, b in zip(arrays, scratch):
+                _swap_storage(a, b)
+            return
         _check(pos, "pos", torch.float64, (3, self.n), self.device)
         ptrs, nbytes = [], []
         for c in carry:
@@ -164,6 +185,43 @@ class ShortRange:
                              perm_out.data_ptr() if perm_out is not None else 0,
                              subtile_id_out.data_ptr() if subtile_id_out is not None else 0)
         self._raise(st)
+
+    def _carry_ptrs(self, carry, name):
+        ptrs, nbytes = [], []
+        for c in carry:
+            _check(c, name, device=self.device)
+            if c.numel() % max(self.n, 1) != 0 and self.n > 0:
+                raise ValueError("carry tensors must hold n elements (any trailing shape)")
+            if c.dim() == 2 and c.shape[0] == 3 and c.shape[1] == self.n and self.n > 0:
+                es = c.element_size()
+                for d in range(3):
+                    ptrs.append(c[d].data_ptr())
+                    nbytes.append(es)
+            else:
+                ptrs.append(c.data_ptr())
+                nbytes.append(c.element_size() * (c.numel() // max(self.n, 1)))
+        return ptrs, nbytes
+
+    def sort_into(self, pos: torch.Tensor, pos_out: torch.Tensor, carry=(), carry_out=(),
+                  perm_out: torch.Tensor | None = None, subtile_id_out: torch.Tensor | None = None):
+        """Out-of-place sort (p3m_sr_sort_into): pos_out and carry_out receive the sorted
+        copies of pos and carry; the inputs are unchanged."""
+        _check(pos, "pos", torch.float64, (3, self.n), self.device)
+        _check(pos_out, "pos_out", torch.float64, (3, self.n), self.device)
+        if len(carry) != len(carry_out):
+            raise ValueError("carry and carry_out must pair up")
+        for a, b in zip(carry, carry_out):
+            if a.dtype != b.dtype or a.shape != b.shape:
+                raise ValueError("carry_out must match carry in dtype and shape")
+        pin, nb = self._carry_ptrs(carry, "carry")
+        pout, _ = self._carry_ptrs(carry_out, "carry_out")
+        if perm_out is not None:
+            _check(perm_out, "perm_out", torch.int32, (self.n,), self.device)
+        if subtile_id_out is not None:
+            _check(subtile_id_out, "subtile_id_out", torch.int32, (self.n,), self.device)
+        self._raise(nat.p3m_sr_sort_into(self._ctx, pos.data_ptr(), pos_out.data_ptr(), pin, pout, nb,
+                                         perm_out.data_ptr() if perm_out is not None else 0,
+                                         subtile_id_out.data_ptr() if subtile_id_out is not None else 0))
 
     def build_pairs(self, rung: torch.Tensor | None = None, rung_min: int = 0):
         if rung is not None:

@@ -79,6 +79,56 @@ def test_sort_bitexact_and_stable():
     sr.close()
 
 
+@pytest.mark.parametrize("wname", ["n32k", "n2m"])
+def test_sort_into_equals_the_in_place_sort(wname):
+    """The out-of-place sort gives the in-place sort's order, positions, records and
+    carried arrays bit for bit and leaves its inputs unchanged; the forces that follow
+    it, also after a drift of its output, equal the oracle's."""
+    from paper_2112_01508_gb300 import ShortRange
+    w = synth.workload(wname)
+    pos = synth.workload_positions(w)
+    n = w.n
+    rng = np.random.default_rng(3)
+    mom = rng.normal(size=(3, n))
+    rung = rng.integers(0, 8, n).astype(np.int8)
+    tag = np.arange(n, dtype=np.int64)
+    with ShortRange.from_workload(w) as sr:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        p_in, m_in, r_in, t_in = dev(pos), dev(mom), dev(rung), dev(tag)
+        p_out, m_out = torch.empty_like(p_in), torch.empty_like(m_in)
+        r_out, t_out = torch.empty_like(r_in), torch.empty_like(t_in)
+        perm2 = torch.empty(n, dtype=torch.int32, device="cuda")
+        ids2 = torch.empty(n, dtype=torch.int32, device="cuda")
+        sr.sort_into(p_in, p_out, [m_in, r_in, t_in], [m_out, r_out, t_out], perm_out=perm2, subtile_id_out=ids2)
+        sr.build_pairs()
+        a_into = sr.forces(p_out, 64)
+        pairs_into = sr.stats().pairs_last
+        # the in-place sort of copies of the same inputs
+        p1, m1, r1, t1 = p_in.clone(), m_in.clone(), r_in.clone(), t_in.clone()
+        perm1 = torch.empty(n, dtype=torch.int32, device="cuda")
+        ids1 = torch.empty(n, dtype=torch.int32, device="cuda")
+        sr.sort(p1, carry=[m1, r1, t1], perm_out=perm1, subtile_id_out=ids1)
+        sr.sync()
+        for a, b in ((p_out, p1), (m_out, m1), (r_out, r1), (t_out, t1), (perm2, perm1), (ids2, ids1)):
+            assert torch.equal(a, b)
+        np.testing.assert_array_equal(p_in.cpu().numpy(), pos)  # inputs unchanged
+        np.testing.assert_array_equal(r_in.cpu().numpy(), rung)
+        # a drift of the output keeps the sort of sort_into usable
+        sr.sort_into(p_in, p_out, [m_in], [m_out])
+        sr.drift(p_out, m_out, 2e-4 * w.x_r)
+        sr.build_pairs()
+        a_drift = sr.forces(p_out, 64)
+        pairs_drift = sr.stats().pairs_last
+        moved = p_out.cpu().numpy()
+    if wname == "n32k":
+        ref, ref_pairs = oracle.sr_accel(pos[:, perm1.cpu().numpy()], w.x_s, w.x_r, w.G_m, "bspline", w.eps)
+        assert pairs_into == ref_pairs
+        assert rel_rms(a_into.cpu().numpy(), ref) <= FP64_TOL
+        ref2, ref2_pairs = oracle.sr_accel(moved, w.x_s, w.x_r, w.G_m, "bspline", w.eps)
+        assert pairs_drift == ref2_pairs
+        assert rel_rms(a_drift.cpu().numpy(), ref2) <= FP64_TOL
+
+
 @pytest.mark.parametrize("rung_min", [0, 3, 7])
 def test_active_rungs(n32k, rung_min):
     pos, _ = n32k
