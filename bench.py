@@ -56,10 +56,12 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 18, help="receivers in the CPU-oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1 << 14, help="receivers per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--evolve", type=int, default=0,
+                    help="profiling modes: benchmark steps applied to the set before the measurement")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 512^3 and 1024^3 sub-records (full step, rung substeps, FP32 vs FP64)")
     ap.add_argument("--only", choices=["forces32", "forces32_gather", "forces64", "vjp32", "sort", "pm32",
-                                       "rung_steps", "kick"],
+                                       "rung_steps", "kick", "substep"],
                     default=None,
                     help="profiling mode: run just one kernel family (no contract line)")
     return ap.parse_args()
@@ -938,6 +940,41 @@ def run_only(args):
             st = sr.stats()
             res[f"deepest_rung_fp{prec}"] = {"kernel_ms": ts, "pairs": st.pairs_last, "receivers": st.n_active}
         print(json.dumps(res))
+        sr.close()
+        return
+    if args.evolve:
+        # the state after some benchmark steps (fake-kick step, then sort, forces, rungs+kick+drift)
+        mom = torch.zeros((3, w.n), dtype=torch.float64, device=dev)
+        rung0 = torch.zeros(w.n, dtype=torch.int8, device=dev)
+        sr.forces(pos, 64, acc64)
+        amag = torch.linalg.vector_norm(acc64, dim=0)
+        gen = torch.Generator(device=dev).manual_seed(0)
+        q99 = float(torch.quantile(amag[torch.randperm(w.n, device=dev, generator=gen)[:1 << 20]].float(), 0.99))
+        dt = 64.0 * (2.0 * 0.025 * w.eps / q99) ** 0.5
+        for _ in range(args.evolve):
+            sr.sort(pos, carry=[mom, rung0])
+            sr.build_pairs()
+            sr.forces(pos, 32, acc32)
+            sr.kick_drift(pos, mom, acc32, rung0, dt, 0.025, w.eps, [dt / 2 ** l for l in range(8)], dt / 128)
+        sr.sort(pos)
+        sr.build_pairs()
+        del mom, rung0
+    if args.only == "substep":
+        # a deep-rung substep: receivers on rung 7 of a fake kick whose step puts ~12% of
+        # the particles there (Eq. rung); all particles supply
+        sr.forces(pos, 32, acc32)
+        amag = torch.linalg.vector_norm(acc32, dim=0)
+        gen = torch.Generator(device=dev).manual_seed(0)
+        q = float(torch.quantile(amag[torch.randperm(w.n, device=dev, generator=gen)[:1 << 20]], 0.88))
+        rung = sr.assign_rungs(acc32, 64.0 * (2.0 * 0.025 * w.eps / q) ** 0.5, 0.025, w.eps)
+        sr.build_pairs(rung, 7)
+        for k in range(args.warmup + args.steps):
+            sr.forces(pos, 32, acc32)
+            st = sr.stats()
+            if k >= args.warmup:
+                times.append(st.force_kernel_ms)
+        print(json.dumps({"only": args.only, "workload": w.name, "kernel_ms": times, "pairs": st.pairs_last,
+                          "receivers": st.n_active, "chunks": st.n_chunks}))
         sr.close()
         return
     if args.only == "kick":
