@@ -322,6 +322,19 @@ p3m_status p3m_sr_rung_kick(p3m_sr_ctx* ctx, void* mom, int mom_precision, const
                             double eta, double eps, int synchronize);
 
 /*
+ * p3m_sr_rung_kick (synchronize = 0) followed by p3m_sr_drift of every particle,
+ * in one pass over the particle arrays (the kick of substep k of the rung-based
+ * leapfrog and the drift that starts substep k + 1, Section 2.2.2): the results
+ * equal those two calls bit for bit.
+ *   pos, drift_factor  as for p3m_sr_drift (drifting the sorted array keeps the
+ *                      sort usable, as p3m_sr_drift does); the other arguments as
+ *                      for p3m_sr_rung_kick.
+ */
+p3m_status p3m_sr_rung_kick_drift(p3m_sr_ctx* ctx, void* mom, int mom_precision, const void* acc, int acc_precision,
+                                  int8_t* rung, int8_t* kick_state, int rung_min, long long substep, double dt,
+                                  double eta, double eps, double* pos, double drift_factor);
+
+/*
  * Drift (Section 2.2.2, operator D with a = 1):
  *   x_i <- x_i + q_i * factor, then wrapped into [0, L): x <- x - L floor(x / L).
  *   pos  3 x n float64 device;  mom  3 x n device, mom_precision 32 or 64.

@@ -35,7 +35,7 @@ EXPORTS = (
     "p3m_sr_build_pairs", "p3m_sr_forces", "p3m_sr_assign_rungs", "p3m_sr_kick", "p3m_sr_drift", "p3m_sr_vjp",
     "p3m_sr_permute", "p3m_sr_unpermute", "p3m_sr_forces_noalloc", "p3m_sr_forces_tabulated",
     "p3m_sr_rung_kick", "p3m_sr_set_subtiles", "p3m_sr_set_symmetric", "p3m_sr_kick_drift",
-    "p3m_sr_set_count", "p3m_sr_tile_offsets", "p3m_sr_sort_into",
+    "p3m_sr_set_count", "p3m_sr_tile_offsets", "p3m_sr_sort_into", "p3m_sr_rung_kick_drift",
 )
 
 
@@ -129,6 +129,8 @@ def load() -> ctypes.CDLL:
         L.p3m_sr_forces_tabulated.restype = i
         L.p3m_sr_rung_kick.argtypes = [p, p, i, p, i, p, p, i, ctypes.c_longlong, d, d, d, i]
         L.p3m_sr_rung_kick.restype = i
+        L.p3m_sr_rung_kick_drift.argtypes = [p, p, i, p, i, p, p, i, ctypes.c_longlong, d, d, d, p, d]
+        L.p3m_sr_rung_kick_drift.restype = i
         L.p3m_sr_set_subtiles.argtypes = [p, ctypes.POINTER(i)]
         L.p3m_sr_set_subtiles.restype = i
         L.p3m_sr_set_symmetric.argtypes = [p, i]
@@ -371,3 +373,11 @@ def p3m_sr_sort_into(ctx, pos_in, pos_out, carry_in, carry_out, carry_bytes, per
     cb = (ctypes.c_int * max(k, 1))(*carry_bytes)
     return load().p3m_sr_sort_into(ctx, ctypes.c_void_p(pos_in), ctypes.c_void_p(pos_out), ci, co, cb, k,
                                    ctypes.c_void_p(perm_ptr or 0), ctypes.c_void_p(ids_ptr or 0))
+
+
+def p3m_sr_rung_kick_drift(ctx, mom_ptr, mom_precision, acc_ptr, acc_precision, rung_ptr, state_ptr, rung_min,
+                           substep, dt, eta, eps, pos_ptr, drift_factor) -> int:
+    return load().p3m_sr_rung_kick_drift(ctx, ctypes.c_void_p(mom_ptr), int(mom_precision), ctypes.c_void_p(acc_ptr),
+                                         int(acc_precision), ctypes.c_void_p(rung_ptr), ctypes.c_void_p(state_ptr),
+                                         int(rung_min), int(substep), float(dt), float(eta), float(eps),
+                                         ctypes.c_void_p(pos_ptr), float(drift_factor))

@@ -112,8 +112,11 @@ __global__ void k_gather_pos(const double* __restrict__ src, const int* __restri
 // ---- launch helpers (host) --------------------------------------------------
 
 // Exclusive scan of n int32 values (in may equal out).  Returns cudaError.
-// Adds the number of kernels it launched to *launches.
-cudaError_t scan_exclusive_i32(const int* in, int* out, int64_t n, int* scratch, cudaStream_t s, int64_t* launches);
+// scratch: scratch_ints >= scan_scratch_ints(n) ints whose last int is zero before
+// the first scan (and is left zero).  Adds the number of kernels it launched to
+// *launches.
+cudaError_t scan_exclusive_i32(const int* in, int* out, int64_t n, int* scratch, int64_t scratch_ints, cudaStream_t s,
+                               int64_t* launches);
 // Scratch (ints) needed by scan_exclusive_i32 for n elements.
 int64_t scan_scratch_ints(int64_t n);
 

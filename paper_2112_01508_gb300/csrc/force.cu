@@ -75,24 +75,66 @@ __global__ void k_rel4(const double* __restrict__ pos, const int* __restrict__ c
   rel4[i] = make_float4((float)r[0], (float)r[1], (float)r[2], __int_as_float(id));
 }
 
-__global__ void k_active_flags(const int8_t* __restrict__ rung, int64_t n, int rung_min, int8_t* __restrict__ flag,
-                               int* __restrict__ act) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > n) return;
-  if (i == n) {
-    act[n] = 0;
-    return;
+// The receiver set in two passes over tiles of kActTile sorted particles: the number
+// of receivers (rung >= rung_min) per tile, then (after a scan of those counts) each
+// tile's flags, its exclusive scan act_scan[0..n] and the compacted receiver list.
+constexpr int kActThreads = 256;
+constexpr int kActItems = 16;
+constexpr int kActTile = kActThreads * kActItems;
+
+__global__ void __launch_bounds__(kActThreads) k_active_count(const int8_t* __restrict__ rung, int64_t n, int rung_min,
+                                                              int* __restrict__ tile_count) {
+  __shared__ int warp_sums[kActThreads / kWarp];
+  const int64_t base = (int64_t)blockIdx.x * kActTile;
+  int c = 0;
+  for (int k = 0; k < kActItems; ++k) {
+    const int64_t i = base + (int64_t)k * kActThreads + threadIdx.x;
+    if (i < n) c += rung[i] >= rung_min ? 1 : 0;
   }
-  int a = rung ? (rung[i] >= rung_min) : 1;
-  flag[i] = (int8_t)a;
-  act[i] = a;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kActThreads / kWarp; ++w) t += warp_sums[w];
+    tile_count[blockIdx.x] = t;
+  }
 }
 
-__global__ void k_compact(const int8_t* __restrict__ flag, const int* __restrict__ act_scan, int64_t n,
-                          int* __restrict__ active_idx) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (flag[i]) active_idx[act_scan[i]] = (int)i;
+__global__ void __launch_bounds__(kActThreads) k_active_scan_compact(const int8_t* __restrict__ rung, int64_t n,
+                                                                     int rung_min, const int* __restrict__ tile_base,
+                                                                     int8_t* __restrict__ flag, int* __restrict__ act_scan,
+                                                                     int* __restrict__ active_idx) {
+  __shared__ int warp_tot[kActThreads / kWarp];
+  const int64_t base = (int64_t)blockIdx.x * kActTile + (int64_t)threadIdx.x * kActItems;  // 16 consecutive items
+  int f[kActItems];
+  int tot = 0;
+#pragma unroll
+  for (int k = 0; k < kActItems; ++k) {
+    const int64_t i = base + k;
+    f[k] = (i < n && rung[i] >= rung_min) ? 1 : 0;
+    tot += f[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = tot;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  int run = inc - tot + tile_base[blockIdx.x];
+  for (int w = 0; w < warp; ++w) run += warp_tot[w];
+#pragma unroll
+  for (int k = 0; k < kActItems; ++k) {
+    const int64_t i = base + k;
+    if (i <= n) act_scan[i] = run;
+    if (i < n) {
+      flag[i] = (int8_t)f[k];
+      if (f[k]) active_idx[run] = (int)i;
+    }
+    run += f[k];
+  }
 }
 
 // Receiver chunks.  The receivers of one row of tiles (fixed tile x, y) are
@@ -1694,7 +1736,8 @@ static p3m_status build_chunks(p3m_sr_ctx* ctx, const int* act_scan, Chunk* chun
                                                          ctx->tile_chunks, ctx->seg_bucket, ctx->bucket_cursor);
   ++ctx->launches;
   if ((st = cuda_check(ctx, cudaGetLastError(), "row chunk kernel")) != P3M_OK) return st;
-  st = cuda_check(ctx, scan_exclusive_i32(ctx->tile_chunks, ctx->tile_chunks, rows + 1, ctx->scan_scratch, s,
+  st = cuda_check(ctx, scan_exclusive_i32(ctx->tile_chunks, ctx->tile_chunks, rows + 1, ctx->scan_scratch,
+                                          ctx->scan_scratch_ints, s,
                                           &ctx->launches), "chunk scan");
   if (st != P3M_OK) return st;
   k_bucket_offsets<<<1, kCostBuckets, 0, s>>>(ctx->bucket_cursor);
@@ -1754,16 +1797,19 @@ extern "C" p3m_status p3m_sr_build_pairs(p3m_sr_ctx* ctx, const int8_t* rung, in
   ctx->all_active = (rung == nullptr);
   const int* act_scan = nullptr;
   if (!ctx->all_active) {
-    k_active_flags<<<blocks_for(n + 1, 256), 256, 0, s>>>(rung, n, rung_min, ctx->active_flag, ctx->act_scan);
-  ++ctx->launches;
-    if ((st = cuda_check(ctx, cudaGetLastError(), "active flags")) != P3M_OK) return st;
-    st = cuda_check(ctx, scan_exclusive_i32(ctx->act_scan, ctx->act_scan, n + 1, ctx->scan_scratch, s, &ctx->launches), "scan");
+    // receivers per tile of sorted particles, scanned, then flags + act_scan + list in one pass
+    const int64_t tiles = (n + 1 + kActTile - 1) / kActTile;  // act_scan has n + 1 entries
+    int* tile_count = ctx->hist;                                // idle outside the sort (>= 1024 per radix tile)
+    k_active_count<<<(unsigned)tiles, kActThreads, 0, s>>>(rung, n, rung_min, tile_count);
+    ++ctx->launches;
+    if ((st = cuda_check(ctx, cudaGetLastError(), "active count")) != P3M_OK) return st;
+    st = cuda_check(ctx, scan_exclusive_i32(tile_count, tile_count, tiles, ctx->scan_scratch, ctx->scan_scratch_ints, s,
+                                            &ctx->launches), "scan");
     if (st != P3M_OK) return st;
-    if (n > 0) {
-      k_compact<<<blocks_for(n, 256), 256, 0, s>>>(ctx->active_flag, ctx->act_scan, n, ctx->active_idx);
-  ++ctx->launches;
-      if ((st = cuda_check(ctx, cudaGetLastError(), "compact")) != P3M_OK) return st;
-    }
+    k_active_scan_compact<<<(unsigned)tiles, kActThreads, 0, s>>>(rung, n, rung_min, tile_count, ctx->active_flag,
+                                                                   ctx->act_scan, ctx->active_idx);
+    ++ctx->launches;
+    if ((st = cuda_check(ctx, cudaGetLastError(), "active scan")) != P3M_OK) return st;
     act_scan = ctx->act_scan;
   }
   st = build_chunks(ctx, act_scan, ctx->chunks, ctx->order, ctx->dev_small + 0, ctx->dev_small + 2);
@@ -1978,6 +2024,7 @@ constexpr int64_t kNoallocRadixBlocks = (kNoallocMaxN + kRadixTilePublic - 1) / 
 constexpr int64_t kNoallocMaxChunks = kNoallocMaxN + kNoallocMaxN / kChunk + 1;
 
 constexpr int64_t noalloc_align(int64_t b) { return (b + 255) / 256 * 256; }
+constexpr int64_t kNoallocScanInts = 4096;  // scan scratch; its last int is the scan's ticket
 
 // Byte layout of the scratch array (each part 256-byte aligned).
 struct NoallocLayout {
@@ -1988,7 +2035,7 @@ struct NoallocLayout {
   static constexpr int64_t offsets = vals1 + noalloc_align(4 * kNoallocMaxN);
   static constexpr int64_t hist = offsets + noalloc_align(4 * (kNoallocMaxSubtiles + 1));
   static constexpr int64_t scan = hist + noalloc_align(4 * 1024 * kNoallocRadixBlocks);
-  static constexpr int64_t wpos = scan + noalloc_align(4 * 4096);
+  static constexpr int64_t wpos = scan + noalloc_align(4 * kNoallocScanInts);
   static constexpr int64_t bad = wpos + noalloc_align(8 * 3 * kNoallocMaxN);
   static constexpr int64_t pos = bad + noalloc_align(kNoallocMaxN);
   static constexpr int64_t rel4 = pos + noalloc_align(8 * 3 * kNoallocMaxN);
@@ -2126,11 +2173,12 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
   // periodic wrap, then bin + subtile offsets (histogram, exclusive scan)
   if (!ok(cudaMemsetAsync(offsets, 0, sizeof(int) * (g.S + 1), s))) return P3M_ERR_CUDA;
   if (!ok(cudaMemsetAsync(small, 0, 64, s))) return P3M_ERR_CUDA;
+  if (!ok(cudaMemsetAsync(scan + kNoallocScanInts - 1, 0, sizeof(int), s))) return P3M_ERR_CUDA;
   k_noalloc_wrap<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, g.box, wpos, bad);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   k_bin<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(wpos, n, g, keys[0], vals[0], offsets, small + 2);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
-  if (!ok(scan_exclusive_i32(offsets, offsets, g.S + 1, scan, s, &launches))) return P3M_ERR_CUDA;
+  if (!ok(scan_exclusive_i32(offsets, offsets, g.S + 1, scan, kNoallocScanInts, s, &launches))) return P3M_ERR_CUDA;
   // stable LSD radix sort of the subtile ids
   int key_bits = 1;
   while (key_bits < 31 && ((int64_t)1 << key_bits) < g.S) ++key_bits;
@@ -2142,7 +2190,7 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
     left -= bits;
     k_radix_hist<<<nblocks, kRadixThreadsPublic, 0, s>>>(keys[cur], n, shift, bits, hist, nblocks);
     if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
-    if (!ok(scan_exclusive_i32(hist, hist, (int64_t)nblocks << bits, scan, s, &launches))) return P3M_ERR_CUDA;
+    if (!ok(scan_exclusive_i32(hist, hist, (int64_t)nblocks << bits, scan, kNoallocScanInts, s, &launches))) return P3M_ERR_CUDA;
     k_radix_scatter<<<nblocks, kRadixThreadsPublic, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n,
                                                             shift, bits, hist, nblocks, nullptr, 0, 0);
     if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
@@ -2159,7 +2207,7 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
   k_row_chunks<<<(unsigned)((nrows + 1 + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows, nullptr,
                                                                    nullptr);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
-  if (!ok(scan_exclusive_i32(rows, rows, nrows + 1, scan, s, &launches))) return P3M_ERR_CUDA;
+  if (!ok(scan_exclusive_i32(rows, rows, nrows + 1, scan, kNoallocScanInts, s, &launches))) return P3M_ERR_CUDA;
   k_write_chunks<<<(unsigned)((nrows + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows, chunks,
                                                                  small + 0, nullptr, n, nullptr, nullptr, nullptr);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;

@@ -119,6 +119,65 @@ __global__ void k_scan_tile(const int* in, int* out, int64_t n, const int* __res
   }
 }
 
+// Exclusive scan of the nb <= kScanTile values of v in place, by one block.
+__device__ __forceinline__ void block_scan_small(volatile int* v, int nb) {
+  __shared__ int warp_tot[kScanThreads / kWarp];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  int vals[kScanItems];
+  int tot = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int i = t * kScanItems + k;
+    vals[k] = i < nb ? v[i] : 0;
+    tot += vals[k];
+  }
+  int inc = tot;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  int run = inc - tot;
+  for (int w = 0; w < warp; ++w) run += warp_tot[w];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int i = t * kScanItems + k;
+    if (i < nb) v[i] = run;
+    run += vals[k];
+  }
+}
+
+// Tile sums, and in the same launch their exclusive scan by the block that finishes
+// last (an atomic ticket; no block waits for another).  *ticket is 0 on entry and
+// is reset to 0 by the last block.
+__global__ void k_scan_reduce_last(const int* __restrict__ in, int64_t n, int* sums, int* ticket) {
+  __shared__ int warp_sums[kScanThreads / kWarp];
+  __shared__ bool last;
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int v = 0;
+    for (int w = 0; w < kScanThreads / kWarp; ++w) v += warp_sums[w];
+    sums[blockIdx.x] = v;
+    __threadfence();
+    last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    block_scan_small(sums, (int)gridDim.x);
+    if (threadIdx.x == 0) *ticket = 0;
+  }
+}
+
 int64_t scan_scratch_ints(int64_t n) {
   int64_t total = 0;
   int64_t m = n;
@@ -126,10 +185,12 @@ int64_t scan_scratch_ints(int64_t n) {
     m = (m + kScanTile - 1) / kScanTile;
     total += m;
   }
-  return total + 1;
+  return total + 2;  // + the ticket of k_scan_reduce_last
 }
 
-cudaError_t scan_exclusive_i32(const int* in, int* out, int64_t n, int* scratch, cudaStream_t s, int64_t* launches) {
+// The ticket lives in the last int of the scratch that scan_scratch_ints(n) sized.
+static cudaError_t scan_rec(const int* in, int* out, int64_t n, int* scratch, int* ticket, cudaStream_t s,
+                            int64_t* launches) {
   if (n <= 0) return cudaSuccess;
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   if (nb == 1) {
@@ -138,13 +199,23 @@ cudaError_t scan_exclusive_i32(const int* in, int* out, int64_t n, int* scratch,
     return cudaGetLastError();
   }
   int* sums = scratch;
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
-  ++*launches;
-  cudaError_t e = scan_exclusive_i32(sums, sums, nb, scratch + nb, s, launches);
-  if (e != cudaSuccess) return e;
+  if (nb <= kScanTile) {  // two launches: tile sums scanned by the last block, then the tiles
+    k_scan_reduce_last<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums, ticket);
+    ++*launches;
+  } else {
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+    ++*launches;
+    cudaError_t e = scan_rec(sums, sums, nb, scratch + nb, ticket, s, launches);
+    if (e != cudaSuccess) return e;
+  }
   k_scan_tile<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
   ++*launches;
   return cudaGetLastError();
+}
+
+cudaError_t scan_exclusive_i32(const int* in, int* out, int64_t n, int* scratch, int64_t scratch_ints, cudaStream_t s,
+                               int64_t* launches) {
+  return scan_rec(in, out, n, scratch, scratch + scratch_ints - 1, s, launches);
 }
 
 }  // namespace p3m
@@ -337,6 +408,9 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
     }
   if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), ctx->stream), "memset")) != P3M_OK)
     goto fail_alloc;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->scan_scratch, 0, sizeof(int) * ctx->scan_scratch_ints, ctx->stream),
+                       "memset")) != P3M_OK)
+    goto fail_alloc;
   if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->drift_slots, 0, sizeof(float) * kMaxDrifts, ctx->stream),
                        "memset")) != P3M_OK)
     goto fail_alloc;
@@ -405,6 +479,8 @@ extern "C" p3m_status p3m_sr_set_subtiles(p3m_sr_ctx* ctx, const int* n_sub) {
     cudaFree(ctx->scan_scratch);
     ctx->scan_scratch = new_scan;
     ctx->scan_scratch_ints = scan_ints;
+    if ((st = cuda_check(ctx, cudaMemsetAsync(new_scan, 0, sizeof(int) * scan_ints, ctx->stream), "memset")) != P3M_OK)
+      return st;
   }
   setup_radix(ctx);
   ctx->sorted = false;

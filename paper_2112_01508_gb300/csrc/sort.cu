@@ -323,7 +323,8 @@ static p3m_status bin_and_sort_ids(p3m_sr_ctx* ctx, const double* pos) {
     ++ctx->launches;
     if ((st = cuda_check(ctx, cudaGetLastError(), "bin kernel")) != P3M_OK) return st;
   }
-  st = cuda_check(ctx, scan_exclusive_i32(ctx->offsets, ctx->offsets, g.S + 1, ctx->scan_scratch, s, &ctx->launches),
+  st = cuda_check(ctx, scan_exclusive_i32(ctx->offsets, ctx->offsets, g.S + 1, ctx->scan_scratch,
+                                          ctx->scan_scratch_ints, s, &ctx->launches),
                   "scan");
   if (st != P3M_OK) return st;
   int cur = 0;
@@ -332,7 +333,8 @@ static p3m_status bin_and_sort_ids(p3m_sr_ctx* ctx, const double* pos) {
     for (int p = 0; p < ctx->radix_passes; ++p) {
       const int bits = ctx->radix_bits[p];
       const bool more = p + 1 < ctx->radix_passes;
-      st = cuda_check(ctx, scan_exclusive_i32(hist[p & 1], hist[p & 1], (int64_t)nblocks << bits, ctx->scan_scratch, s,
+      st = cuda_check(ctx, scan_exclusive_i32(hist[p & 1], hist[p & 1], (int64_t)nblocks << bits, ctx->scan_scratch,
+                                              ctx->scan_scratch_ints, s,
                                               &ctx->launches), "radix scan");
       if (st != P3M_OK) return st;
       int* next = more ? hist[(p + 1) & 1] : nullptr;

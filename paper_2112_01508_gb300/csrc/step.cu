@@ -179,13 +179,13 @@ __global__ void __launch_bounds__(256) k_kick_drift(double* __restrict__ pos, M*
   }
 }
 
-// One kick of the rung-based leapfrog with the rung update (see p3m_sr_rung_kick).
+// One kick of the rung-based leapfrog with the rung update (see p3m_sr_rung_kick) for
+// particle i.
 template <class M, class A>
-__global__ void k_rung_kick(M* __restrict__ mom, const A* __restrict__ acc, int8_t* __restrict__ rung,
-                            int8_t* __restrict__ state, int64_t n, int rung_min, long long k, int log2_sub, double dt,
-                            double qq, float qqf, int n_rung, int sync, int* __restrict__ err) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void rung_kick_one(M* __restrict__ mom, const A* __restrict__ acc, int8_t* __restrict__ rung,
+                                              int8_t* __restrict__ state, int64_t n, int64_t i, int rung_min,
+                                              long long k, int log2_sub, double dt, double qq, float qqf, int n_rung,
+                                              int sync, int* __restrict__ err) {
   const int l = rung[i];
   if (l < rung_min) return;
   const int st = state[i];
@@ -218,6 +218,58 @@ __global__ void k_rung_kick(M* __restrict__ mom, const A* __restrict__ acc, int8
   }
   rung[i] = (int8_t)out;
   state[i] = (int8_t)ost;
+}
+
+template <class M, class A>
+__global__ void k_rung_kick(M* __restrict__ mom, const A* __restrict__ acc, int8_t* __restrict__ rung,
+                            int8_t* __restrict__ state, int64_t n, int rung_min, long long k, int log2_sub, double dt,
+                            double qq, float qqf, int n_rung, int sync, int* __restrict__ err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  rung_kick_one<M, A>(mom, acc, rung, state, n, i, rung_min, k, log2_sub, dt, qq, qqf, n_rung, sync, err);
+}
+
+// A rung kick followed by the drift of every particle, in one pass (the results of
+// k_rung_kick then k_drift, bit for bit; disp as in k_drift).
+template <class M, class A>
+__global__ void __launch_bounds__(256) k_rung_kick_drift(M* __restrict__ mom, const A* __restrict__ acc,
+                                                         int8_t* __restrict__ rung, int8_t* __restrict__ state,
+                                                         int64_t n, int rung_min, long long k, int log2_sub, double dt,
+                                                         double qq, float qqf, int n_rung, int* __restrict__ err,
+                                                         double* __restrict__ pos, double factor, double box,
+                                                         float* __restrict__ disp) {
+  __shared__ unsigned warp_max[8];
+  float my = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    rung_kick_one<M, A>(mom, acc, rung, state, n, i, rung_min, k, log2_sub, dt, qq, qqf, n_rung, 0, err);
+    float q2 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double q = (double)mom[d * n + i];
+      const float qf = (float)q;
+      q2 = fmaf(qf, qf, q2);
+      double v = __dadd_rn(pos[d * n + i], __dmul_rn(q, factor));
+      const long long vb = __double_as_longlong(v);
+      if (!(vb >= 0 && vb < __double_as_longlong(box))) {
+        v = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
+        if (v >= box || v < 0.0) v = 0.0;
+      }
+      pos[d * n + i] = v;
+    }
+    float di = sqrtf(q2) * (float)fabs(factor) * 1.0001f;
+    if (!(di < 3.0e38f)) di = 3.0e38f;
+    my = fmaxf(my, di);
+  }
+  if (disp) {
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(my));
+    if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned b = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = max(b, warp_max[w]);
+      if (b) atomicMax((unsigned*)disp, b);
+    }
+  }
 }
 
 // Drifting the sorted positions keeps the sort usable: the displacement bound of
@@ -373,9 +425,31 @@ extern "C" p3m_status p3m_sr_drift(p3m_sr_ctx* ctx, double* pos, const void* mom
   return cuda_check(ctx, cudaGetLastError(), "drift kernel");
 }
 
+static p3m_status rung_kick_impl(p3m_sr_ctx* ctx, void* mom, int mom_precision, const void* acc, int acc_precision,
+                                 int8_t* rung, int8_t* kick_state, int rung_min, long long substep, double dt,
+                                 double eta, double eps, int synchronize, double* pos, double drift_factor);
+
 extern "C" p3m_status p3m_sr_rung_kick(p3m_sr_ctx* ctx, void* mom, int mom_precision, const void* acc,
                                        int acc_precision, int8_t* rung, int8_t* kick_state, int rung_min,
                                        long long substep, double dt, double eta, double eps, int synchronize) {
+  return rung_kick_impl(ctx, mom, mom_precision, acc, acc_precision, rung, kick_state, rung_min, substep, dt, eta, eps,
+                        synchronize, nullptr, 0.0);
+}
+
+extern "C" p3m_status p3m_sr_rung_kick_drift(p3m_sr_ctx* ctx, void* mom, int mom_precision, const void* acc,
+                                             int acc_precision, int8_t* rung, int8_t* kick_state, int rung_min,
+                                             long long substep, double dt, double eta, double eps, double* pos,
+                                             double drift_factor) {
+  if (!ctx) return P3M_ERR_INVALID;
+  if (ctx->n > 0 && !pos) return fail(ctx, P3M_ERR_INVALID, "rung_kick_drift: null positions");
+  if (!std::isfinite(drift_factor)) return fail(ctx, P3M_ERR_INVALID, "rung_kick_drift: drift_factor must be finite");
+  return rung_kick_impl(ctx, mom, mom_precision, acc, acc_precision, rung, kick_state, rung_min, substep, dt, eta, eps,
+                        0, pos, drift_factor);
+}
+
+static p3m_status rung_kick_impl(p3m_sr_ctx* ctx, void* mom, int mom_precision, const void* acc, int acc_precision,
+                                 int8_t* rung, int8_t* kick_state, int rung_min, long long substep, double dt,
+                                 double eta, double eps, int synchronize, double* pos, double drift_factor) {
   if (!ctx) return P3M_ERR_INVALID;
   if ((mom_precision != 32 && mom_precision != 64) || (acc_precision != 32 && acc_precision != 64))
     return fail(ctx, P3M_ERR_INVALID, "rung_kick: precision must be 32 or 64");
@@ -403,6 +477,32 @@ extern "C" p3m_status p3m_sr_rung_kick(p3m_sr_ctx* ctx, void* mom, int mom_preci
   const int64_t n = ctx->n;
   const int nr = ctx->prm.n_rung;
   const int sy = synchronize ? 1 : 0;
+  if (pos) {  // the kick, then the drift of every particle, in one pass
+    float* slot = drift_slot(ctx, pos);
+    const unsigned bd = (unsigned)std::min<int64_t>(b, (int64_t)ctx->num_sms * 8);
+    const float qqf = rung_qqf(qq);
+    const double L = ctx->prm.box;
+    if (mom_precision == 64 && acc_precision == 32)
+      k_rung_kick_drift<double, float><<<bd, t, 0, s>>>((double*)mom, (const float*)acc, rung, kick_state, n, rung_min,
+                                                        substep, log2_sub, dt, qq, qqf, nr, ctx->err_dev, pos,
+                                                        drift_factor, L, slot);
+    else if (mom_precision == 64 && acc_precision == 64)
+      k_rung_kick_drift<double, double><<<bd, t, 0, s>>>((double*)mom, (const double*)acc, rung, kick_state, n,
+                                                         rung_min, substep, log2_sub, dt, qq, qqf, nr, ctx->err_dev,
+                                                         pos, drift_factor, L, slot);
+    else if (mom_precision == 32 && acc_precision == 32)
+      k_rung_kick_drift<float, float><<<bd, t, 0, s>>>((float*)mom, (const float*)acc, rung, kick_state, n, rung_min,
+                                                       substep, log2_sub, dt, qq, qqf, nr, ctx->err_dev, pos,
+                                                       drift_factor, L, slot);
+    else
+      k_rung_kick_drift<float, double><<<bd, t, 0, s>>>((float*)mom, (const double*)acc, rung, kick_state, n, rung_min,
+                                                        substep, log2_sub, dt, qq, qqf, nr, ctx->err_dev, pos,
+                                                        drift_factor, L, slot);
+    ++ctx->launches;
+    if ((st = cuda_check(ctx, cudaGetLastError(), "rung kick-drift kernel")) != P3M_OK) return st;
+    report_latched(ctx);
+    return P3M_OK;
+  }
   if (mom_precision == 64 && acc_precision == 32)
     k_rung_kick<double, float><<<b, t, 0, s>>>((double*)mom, (const float*)acc, rung, kick_state, n, rung_min, substep,
                                                log2_sub, dt, qq, rung_qqf(qq), nr, sy, ctx->err_dev);

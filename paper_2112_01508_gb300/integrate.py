@@ -63,6 +63,7 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
     acc_lr = None if long_range is None else torch.empty((3, sr.n), dtype=long_range.dtype, device=dev)
     half = [dt / 2.0 ** (l + 1) for l in range(n_rung)]
     k = 0
+    drifted = False  # the drift of the coming substep was applied with the previous kick
     for step in range(n_steps):
         if step % period == 0:
             sr.assign_rungs(acc, dt, eta, eps, rung)
@@ -75,13 +76,20 @@ def rung_leapfrog(sr: ShortRange, pos: torch.Tensor, mom: torch.Tensor, dt: floa
         last_of_period = (step + 1) % period == 0 or step == n_steps - 1
         for s in range(1, sub + 1):
             k += 1
-            sr.drift(pos, mom, dt / sub)
+            if not drifted:
+                sr.drift(pos, mom, dt / sub)
             if k % resort_every == 0:
                 sr.sort(pos, carry=carried, scratch=scratch)
             lmin = substep_rung_min(k, n_rung)
             sr.build_pairs(None if lmin == 0 else rung, lmin)  # lmin 0: all receivers (each pair once in FP32)
             sr.forces(pos, precision, acc)
-            sr.rung_kick(mom, acc, rung, state, lmin, k, dt, eta, eps, synchronize=last_of_period and s == sub)
+            # the kick and the next substep's drift in one pass, unless a synchronisation,
+            # a mesh kick or a new period comes between them
+            drifted = s < sub or (long_range is None and not last_of_period)
+            if drifted:
+                sr.rung_kick_drift(mom, acc, rung, state, lmin, k, dt, eta, eps, pos, dt / sub)
+            else:
+                sr.rung_kick(mom, acc, rung, state, lmin, k, dt, eta, eps, synchronize=last_of_period and s == sub)
             if long_range is not None and s == sub:
                 long_range.accel(pos, acc_lr)
                 sr.kick(mom, acc_lr, [dt / 2.0 if last_of_period else dt])

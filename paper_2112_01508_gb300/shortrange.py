@@ -280,6 +280,20 @@ class ShortRange:
                                          rung.data_ptr(), kick_state.data_ptr(), rung_min, substep, dt, eta, eps,
                                          int(synchronize)))
 
+    def rung_kick_drift(self, mom: torch.Tensor, acc: torch.Tensor, rung: torch.Tensor, kick_state: torch.Tensor,
+                        rung_min: int, substep: int, dt: float, eta: float, eps: float, pos: torch.Tensor,
+                        drift_factor: float):
+        """rung_kick (not synchronising) then drift of every particle, in one pass
+        (p3m_sr_rung_kick_drift; bit for bit the two calls)."""
+        _check(mom, "mom", (torch.float32, torch.float64), (3, self.n), self.device)
+        _check(acc, "acc", (torch.float32, torch.float64), (3, self.n), self.device)
+        _check(rung, "rung", torch.int8, (self.n,), self.device)
+        _check(kick_state, "kick_state", torch.int8, (self.n,), self.device)
+        _check(pos, "pos", torch.float64, (3, self.n), self.device)
+        self._raise(nat.p3m_sr_rung_kick_drift(self._ctx, mom.data_ptr(), _PREC[mom.dtype], acc.data_ptr(),
+                                               _PREC[acc.dtype], rung.data_ptr(), kick_state.data_ptr(), rung_min,
+                                               substep, dt, eta, eps, pos.data_ptr(), drift_factor))
+
     def drift(self, pos: torch.Tensor, mom: torch.Tensor, factor: float):
         _check(pos, "pos", torch.float64, (3, self.n), self.device)
         _check(mom, "mom", (torch.float32, torch.float64), (3, self.n), self.device)

@@ -225,3 +225,35 @@ def test_rung_leapfrog_fp32_momenta_vs_oracle():
     assert dq[clean].max() <= FP32_CYCLE_DQ * Q, dq[clean].max() / Q
     assert rel_rms(d_got[:, clean], d_ref[:, clean]) <= FP32_CYCLE_RMS
     assert rel_rms(got_q[:, clean], q_ref[:, clean]) <= FP32_CYCLE_RMS
+
+
+@pytest.mark.parametrize("mom_dt,acc_dt", [(np.float64, np.float32), (np.float32, np.float64)])
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_rung_kick_drift_equals_kick_then_drift(mom_dt, acc_dt, k):
+    """The fused kick + drift pass gives the momenta, rungs, kick states and positions of
+    p3m_sr_rung_kick followed by p3m_sr_drift, bit for bit."""
+    n, n_rung, dt, eta, eps = 50000, 4, 0.07, 0.025, W.eps
+    rng = np.random.default_rng(40 + k)
+    mag = np.exp(rng.uniform(np.log(1e-3), np.log(1e5), n))
+    acc = rng.normal(size=(3, n))
+    acc = (acc * mag / np.linalg.norm(acc, axis=0)).astype(acc_dt)
+    mom = rng.normal(size=(3, n)).astype(mom_dt)
+    pos = rng.random((3, n))
+    pos[:, :20] = 1.0 - 1e-16  # wraps
+    rung = rng.integers(0, n_rung, n).astype(np.int8)
+    state = rng.integers(0, 3, n).astype(np.int8)
+    tz = 0
+    while tz < n_rung - 1 and (k >> tz) & 1 == 0:
+        tz += 1
+    lmin = n_rung - 1 - tz
+    with ShortRange(n, W.x_s, W.x_r, W.G_m, softening="bspline", eps=eps, n_rung=n_rung) as sr:
+        t = lambda a: torch.from_numpy(a.copy()).cuda()
+        q1, r1, s1, p1 = t(mom), t(rung), t(state), t(pos)
+        sr.rung_kick_drift(q1, t(acc), r1, s1, lmin, k, dt, eta, eps, p1, dt / 8)
+        q2, r2, s2, p2 = t(mom), t(rung), t(state), t(pos)
+        sr.rung_kick(q2, t(acc), r2, s2, lmin, k, dt, eta, eps)
+        sr.drift(p2, q2, dt / 8)
+        sr.sync()
+    for a, b in ((q1, q2), (r1, r2), (s1, s2), (p1, p2)):
+        assert torch.equal(a, b)
+    assert (r1.cpu().numpy() != rung).any()
