@@ -12,7 +12,6 @@ namespace p3m {
 constexpr int kWarp = 32;
 constexpr int kMaxDrifts = 64;  // drifts of the sorted positions allowed between two sorts
 constexpr int kChunk = 32;  // receivers per chunk (one warp lane each)
-constexpr int kCostBuckets = 256;  // chunk cost classes (4 per octave of the estimate)
 constexpr int kPartItems = 32768;  // work items of split chunks that the partial-sum buffer holds
 constexpr int kMaxParts = 8;       // parts a chunk is split into at most
 

@@ -36,10 +36,6 @@ struct p3m_sr_ctx {
   int* act_scan = nullptr;            // n + 1
   int* active_idx = nullptr;          // n
   int* tile_chunks = nullptr;         // n_tiles + 1 (chunks per row segment, scanned)
-  unsigned char* seg_bucket = nullptr;  // n_tiles + 1: cost bucket of each row segment
-  int* bucket_cursor = nullptr;       // p3m::kCostBuckets: chunks per cost bucket, then write cursors
-  int* order = nullptr;               // max_chunks: chunks of `chunks` in decreasing estimated cost
-  int* order_all = nullptr;           // the same for `chunks_all`
   float4* part_acc = nullptr;         // partial sums of split chunks (work items x 32 lanes)
   p3m::Chunk* chunks = nullptr;       // receiver chunks of the last build_pairs
   p3m::Chunk* chunks_all = nullptr;   // chunks over all particles (vjp)

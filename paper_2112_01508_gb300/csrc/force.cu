@@ -165,47 +165,8 @@ __device__ __forceinline__ void segment_range(const int* __restrict__ offsets, c
   a1 = tile_start(offsets, act_scan, nsub3, t1);
 }
 
-// Estimated cost of a chunk of segment `seg`: the particles within one tile of each
-// tile of the segment (summed over its tiles, 3 x 3 x 3 tiles each, periodic).  A
-// chunk's work is its surviving suppliers, which this count follows; it orders the
-// chunks so that the expensive ones start first (longest-processing-time-first).
-__device__ __forceinline__ unsigned long long segment_cost(const int* __restrict__ offsets, int nsub3, int n_t,
-                                                           int64_t seg) {
-  const int nseg = (n_t + kChunkSpan - 1) / kChunkSpan;
-  const int64_t row = seg / nseg;
-  const int k = (int)(seg - row * nseg);
-  const int tx = (int)(row / n_t), ty = (int)(row - (int64_t)tx * n_t);
-  const int tz0 = k * kChunkSpan, tz1 = min(n_t, tz0 + kChunkSpan);
-  unsigned long long est = 0;
-  for (int dx = -1; dx <= 1; ++dx) {
-    const int x = (tx + dx + n_t) % n_t;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int y = (ty + dy + n_t) % n_t;
-      const int64_t base = ((int64_t)x * n_t + y) * n_t;
-      for (int z = tz0 - 1; z <= tz1; ++z) {
-        // weight: the segment tiles within one tile of z along the row
-        const int w = min(z + 1, tz1 - 1) - max(z - 1, tz0) + 1;
-        if (w <= 0) continue;
-        const int zz = (z + n_t) % n_t;
-        const int64_t T = base + zz;
-        est += (unsigned long long)w * (unsigned long long)(offsets[(T + 1) * nsub3] - offsets[T * nsub3]);
-      }
-    }
-  }
-  return est;
-}
-
-__device__ __forceinline__ int cost_bucket(unsigned long long v) {
-  if (v < 4) return (int)v;
-  const int e = 63 - __clzll((long long)v);
-  return min(kCostBuckets - 1, 4 * e + (int)((v >> (e - 2)) & 3) - 4);
-}
-
-// seg_bucket / bucket_count (nullable): the cost bucket of each segment and the
-// number of chunks per bucket (bucket_count zeroed before the launch).
 __global__ void k_row_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int n_t, int nsub3,
-                             int* __restrict__ seg_chunks, unsigned char* __restrict__ seg_bucket,
-                             int* __restrict__ bucket_count) {
+                             int* __restrict__ seg_chunks) {
   const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nsegs = (int64_t)n_t * n_t * ((n_t + kChunkSpan - 1) / kChunkSpan);
   if (seg > nsegs) return;
@@ -215,35 +176,12 @@ __global__ void k_row_chunks(const int* __restrict__ offsets, const int* __restr
   }
   int a0, a1;
   segment_range(offsets, act_scan, nsub3, n_t, seg, a0, a1);
-  const int nc = (a1 - a0 + kChunk - 1) / kChunk;
-  seg_chunks[seg] = nc;
-  if (seg_bucket && nc > 0) {
-    const int b = cost_bucket(segment_cost(offsets, nsub3, n_t, seg));
-    seg_bucket[seg] = (unsigned char)b;
-    atomicAdd(&bucket_count[b], nc);
-  }
+  seg_chunks[seg] = (a1 - a0 + kChunk - 1) / kChunk;
 }
 
-// Chunks per cost bucket -> first position of each bucket in the processing order,
-// the most expensive bucket first (one block of kCostBuckets threads).
-__global__ void k_bucket_offsets(int* __restrict__ bucket) {
-  __shared__ int c[kCostBuckets];
-  const int t = threadIdx.x;
-  c[t] = bucket[t];
-  __syncthreads();
-  int s = 0;
-  for (int u = t + 1; u < kCostBuckets; ++u) s += c[u];
-  bucket[t] = s;
-}
-
-// order (nullable): the chunk indices in decreasing estimated cost (bucket cursors from
-// k_bucket_offsets; the order within a bucket depends on the order of execution, the
-// results do not).
 __global__ void k_write_chunks(const int* __restrict__ offsets, const int* __restrict__ act_scan, int n_t, int nsub3,
                                const int* __restrict__ seg_chunks, Chunk* __restrict__ chunks,
-                               int* __restrict__ n_chunks_out, int* __restrict__ n_active_out, int64_t n,
-                               const unsigned char* __restrict__ seg_bucket, int* __restrict__ bucket_cursor,
-                               int* __restrict__ order) {
+                               int* __restrict__ n_chunks_out, int* __restrict__ n_active_out, int64_t n) {
   const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nsegs = (int64_t)n_t * n_t * ((n_t + kChunkSpan - 1) / kChunkSpan);
   if (seg == 0) {
@@ -253,17 +191,10 @@ __global__ void k_write_chunks(const int* __restrict__ offsets, const int* __res
   if (seg >= nsegs) return;
   int a0, a1;
   segment_range(offsets, act_scan, nsub3, n_t, seg, a0, a1);
-  const int first = seg_chunks[seg];
-  Chunk* out = chunks + first;
-  int nc = 0;
+  Chunk* out = chunks + seg_chunks[seg];
   for (int k = 0; a0 + k * kChunk < a1; ++k) {
     const int s0 = a0 + k * kChunk;
     out[k] = Chunk{s0, min(kChunk, a1 - s0)};
-    ++nc;
-  }
-  if (order && nc > 0) {
-    const int p = atomicAdd(&bucket_cursor[seg_bucket[seg]], nc);
-    for (int k = 0; k < nc; ++k) order[p + k] = first + k;
   }
 }
 
@@ -299,7 +230,6 @@ struct TraversalArgs {
   const int* offsets;         // S + 1 subtile offsets
   const int* cell;            // sorted subtile ids
   const Chunk* chunks;
-  const int* order;           // processing order of the chunks (decreasing estimated cost), or nullptr
   float4* part_acc;           // per (work item, lane) partial sums when chunks are split (kPartItems x 32), or nullptr
   const float* drift_slots;   // displacement bounds of the drifts since the sort (device)
   int n_drift;                // how many of them
@@ -735,19 +665,9 @@ __device__ __forceinline__ int next_chunk(const TraversalArgs& a, int lane) {
   return __shfl_sync(0xffffffffu, c, 0);
 }
 
-// Chunk processing order.  The chunk list is in the sorted (spatial) order, which
-// keeps neighbouring chunks, and the suppliers they share, together in L2.  With
-// few chunks (split into parts, below) the cost-ordered list is used instead so
-// that the most expensive chunks start first.  P3M_LPT: 0 never, 1 with split
-// chunks only, 2 always (tuning builds).
-#ifndef P3M_LPT
-#define P3M_LPT 1
-#endif
-
-// The c-th chunk to process (c < n_chunks).
-__device__ __forceinline__ Chunk chunk_at(const TraversalArgs& a, int c, bool by_cost = P3M_LPT == 2) {
-  return a.chunks[(a.order && by_cost) ? a.order[c] : c];
-}
+// The c-th chunk to process (c < n_chunks): the chunk list is in the sorted, spatial
+// order, which keeps neighbouring chunks, and the suppliers they share, together in L2.
+__device__ __forceinline__ Chunk chunk_at(const TraversalArgs& a, int c) { return a.chunks[c]; }
 
 // Work items per chunk of the one-sided kernel: with few chunks (sparse receivers,
 // the deepest rungs) each chunk's candidate subtiles are split between up to
@@ -815,10 +735,27 @@ __device__ __forceinline__ float fma_sat(float a, float b, float c) {
   return d;
 }
 
+// cp.async of 16 bytes into shared memory (completion per thread, by commit groups)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// As P3M_SYM_CPASYNC for the one-sided kernel (2.087 -> 2.052 ms all active on the
+// 128^3 set).
+#ifndef P3M_GP_CPASYNC
+#define P3M_GP_CPASYNC 1
+#endif
+
 struct PackedSmem {
   WarpList L;
   float4 sxy[kWarp / 2 + 1];  // (-xa, -xb, -ya, -yb)
   float2 sz[kWarp / 2 + 1];   // (-za, -zb)
+#if P3M_GP_CPASYNC
+  float4 rec[2][kWarp];       // records of the current and the next batch
+#endif
 };
 
 // 6 resident blocks of 4 warps per SM bound the kernel to ~80 registers;
@@ -851,7 +788,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
     if (w >= n_items) break;
     const int c = w / nparts, part = w - c * nparts;
     ChunkFrame<float> F;
-    load_chunk<float>(a, rc, chunk_at(a, c, P3M_LPT == 2 || (P3M_LPT == 1 && nparts > 1)), lane, F);
+    load_chunk<float>(a, rc, chunk_at(a, c), lane, F);
     const f2 px = pk(F.pi.x, F.pi.x), py = pk(F.pi.y, F.pi.y), pz = pk(F.pi.z, F.pi.z);
     f2 ax = pk(0.f, 0.f), ay = pk(0.f, 0.f), az = pk(0.f, 0.f);
     f2 hitsf = pk(0.f, 0.f);  // interacting pairs of this lane (exact integers in FP32)
@@ -881,13 +818,27 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
       int jn;
       unsigned dn;
       bool vn = locate(0, jn, dn);
+#if P3M_GP_CPASYNC
+      int buf = 0;
+      if (vn) cp_async16(&S.rec[0][lane], a.rel4 + jn);
+      cp_async_commit();
+#else
       float4 rn = vn ? a.rel4[jn] : make_float4(0.f, 0.f, 0.f, 0.f);
+#endif
       for (int b = 0; b < total; b += kWarp) {
         const bool have = vn;
-        const float4 r = rn;
         const unsigned dpk = dn;
         vn = (b + kWarp < total) ? locate(b + kWarp, jn, dn) : false;
+#if P3M_GP_CPASYNC
+        if (vn) cp_async16(&S.rec[buf ^ 1][lane], a.rel4 + jn);
+        cp_async_commit();
+        cp_async_wait_prev();  // this lane's copy of batch b has landed
+        const float4 r = have ? S.rec[buf][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        buf ^= 1;
+#else
+        const float4 r = rn;
         if (vn) rn = a.rel4[jn];
+#endif
         bool keep = false, near = false;
         Vec3<float> pj = {0.f, 0.f, 0.f};
         if (have) {
@@ -1010,7 +961,7 @@ __global__ void k_parts_finish(TraversalArgs a) {
   const float s = -(float)a.f.G_m;
   float* o = (float*)a.out;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += nw) {
-    const Chunk ch = chunk_at(a, c, P3M_LPT >= 1);
+    const Chunk ch = chunk_at(a, c);
     if (lane >= ch.count) continue;
     const int pidx = a.active_idx ? a.active_idx[ch.start + lane] : ch.start + lane;
     float x = 0.f, y = 0.f, z = 0.f;
@@ -1050,22 +1001,35 @@ __global__ void k_parts_finish(TraversalArgs a) {
 
 constexpr float kSymPad = 1e10f;  // padding supplier at -1e10, invalid receiver at +1e10: finite B, no hit
 
+// Supplier records of the next batch: copied into a per-warp shared-memory double
+// buffer with cp.async while the current batch is staged (1), or prefetched into
+// registers (0).  Measured on the 128^3 set: 1.551 -> 1.518 ms.
+#ifndef P3M_SYM_CPASYNC
+#define P3M_SYM_CPASYNC 1
+#endif
+
 struct SymSmem {
   WarpList L;
   float4 sxy[kWarp];  // pair q: (-x_a, -x_b, -y_a, -y_b) of suppliers a = q and b = q + P
   float2 sz[kWarp];   // (-z_a, -z_b)
   int2 sj[kWarp];     // (j_a, j_b): sorted indices, -1 for padding
   int rq[3 * kWarp];  // forward: pairs closer than r_sw (receiver lane | pair << 5 | half << 10)
+#if P3M_SYM_CPASYNC
+  float4 rec[2][kWarp];  // records of the current and the next batch
+#endif
 };
+
+
 struct SymVjpSmem : SymSmem {
   float4 vxy[kWarp];  // adjoint: the suppliers' masked abar, negated, in the layout of sxy / sz
   float2 vz[kWarp];
 };
 
-// 4 resident blocks of 4 warps per SM leave the kernel 128 registers; measured
-// best on the 128^3 set against 5 and 6 blocks (which spill).
+// 5 resident blocks of 4 warps per SM (96 registers, a few bytes of spills): with the
+// cp.async staging measured best on the 128^3 set (1.490 ms against 1.518 with 4
+// blocks and 128 registers).
 #ifndef P3M_SYM_MINBLOCKS
-#define P3M_SYM_MINBLOCKS 4
+#define P3M_SYM_MINBLOCKS 5
 #endif
 
 __device__ __forceinline__ f2 shfl2(f2 v, int src) {
@@ -1397,7 +1361,14 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
           int jn;
           unsigned dn;
           bool vn = locate(0, jn, dn);
+#if P3M_SYM_CPASYNC
+          int buf = 0;
+          if (vn) cp_async16(&S.rec[0][lane], a.rel4 + jn);
+          cp_async_commit();
+          float4 rn = make_float4(0.f, 0.f, 0.f, 0.f);
+#else
           float4 rn = vn ? a.rel4[jn] : make_float4(0.f, 0.f, 0.f, 0.f);
+#endif
           float4 an = make_float4(0.f, 0.f, 0.f, 0.f);
           if (VJP && vn) an = a.abar4[jn];
           for (int b = 0;; b += kWarp) {
@@ -1408,12 +1379,20 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
             float4 aj = make_float4(0.f, 0.f, 0.f, 0.f);
             if (more) {
               const bool have = vn;
-              const float4 r = rn;
               const unsigned dpk = dn;
               j = jn;
               if (VJP) aj = an;
               vn = (b + kWarp < total) ? locate(b + kWarp, jn, dn) : false;
+#if P3M_SYM_CPASYNC
+              if (vn) cp_async16(&S.rec[buf ^ 1][lane], a.rel4 + jn);
+              cp_async_commit();
+              cp_async_wait_prev();  // this lane's copy of batch b has landed
+              const float4 r = have ? S.rec[buf][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+              buf ^= 1;
+#else
+              const float4 r = rn;
               if (vn) rn = a.rel4[jn];
+#endif
               if (VJP && vn) an = a.abar4[jn];
               if (have) {
                 int ddx, ddy, ddz;
@@ -1724,35 +1703,30 @@ static cudaError_t dispatch_traverse(p3m_sr_ctx* ctx, const TraversalArgs& a) {
   }
 }
 
-// Receiver chunks of the row segments, and their processing order by estimated cost.
-static p3m_status build_chunks(p3m_sr_ctx* ctx, const int* act_scan, Chunk* chunks, int* order, int* n_chunks_dev,
+// Receiver chunks of the row segments.
+static p3m_status build_chunks(p3m_sr_ctx* ctx, const int* act_scan, Chunk* chunks, int* n_chunks_dev,
                                int* n_active_dev) {
   cudaStream_t s = ctx->stream;
   const int n_t = ctx->geo.n_t;
   const int64_t rows = (int64_t)n_t * n_t * ((n_t + kChunkSpan - 1) / kChunkSpan);  // segments
-  p3m_status st = cuda_check(ctx, cudaMemsetAsync(ctx->bucket_cursor, 0, sizeof(int) * kCostBuckets, s), "memset");
-  if (st != P3M_OK) return st;
   k_row_chunks<<<blocks_for(rows + 1, 128), 128, 0, s>>>(ctx->offsets, act_scan, n_t, ctx->geo.nsub3,
-                                                         ctx->tile_chunks, ctx->seg_bucket, ctx->bucket_cursor);
+                                                         ctx->tile_chunks);
   ++ctx->launches;
-  if ((st = cuda_check(ctx, cudaGetLastError(), "row chunk kernel")) != P3M_OK) return st;
-  st = cuda_check(ctx, scan_exclusive_i32(ctx->tile_chunks, ctx->tile_chunks, rows + 1, ctx->scan_scratch,
-                                          ctx->scan_scratch_ints, s,
-                                          &ctx->launches), "chunk scan");
+  p3m_status st = cuda_check(ctx, cudaGetLastError(), "row chunk kernel");
   if (st != P3M_OK) return st;
-  k_bucket_offsets<<<1, kCostBuckets, 0, s>>>(ctx->bucket_cursor);
-  ++ctx->launches;
-  if ((st = cuda_check(ctx, cudaGetLastError(), "bucket offsets kernel")) != P3M_OK) return st;
+  st = cuda_check(ctx, scan_exclusive_i32(ctx->tile_chunks, ctx->tile_chunks, rows + 1, ctx->scan_scratch,
+                                          ctx->scan_scratch_ints, s, &ctx->launches), "chunk scan");
+  if (st != P3M_OK) return st;
   k_write_chunks<<<blocks_for(rows, 128), 128, 0, s>>>(ctx->offsets, act_scan, n_t, ctx->geo.nsub3,
                                                         ctx->tile_chunks, chunks, n_chunks_dev, n_active_dev,
-                                                        ctx->n, ctx->seg_bucket, ctx->bucket_cursor, order);
+                                                        ctx->n);
   ++ctx->launches;
   return cuda_check(ctx, cudaGetLastError(), "write chunks kernel");
 }
 
 p3m_status ensure_all_chunks(p3m_sr_ctx* ctx) {
   if (ctx->all_chunks_built) return P3M_OK;
-  p3m_status st = build_chunks(ctx, nullptr, ctx->chunks_all, ctx->order_all, ctx->dev_small + 1, nullptr);
+  p3m_status st = build_chunks(ctx, nullptr, ctx->chunks_all, ctx->dev_small + 1, nullptr);
   if (st == P3M_OK) ctx->all_chunks_built = true;
   return st;
 }
@@ -1812,7 +1786,7 @@ extern "C" p3m_status p3m_sr_build_pairs(p3m_sr_ctx* ctx, const int8_t* rung, in
     if ((st = cuda_check(ctx, cudaGetLastError(), "active scan")) != P3M_OK) return st;
     act_scan = ctx->act_scan;
   }
-  st = build_chunks(ctx, act_scan, ctx->chunks, ctx->order, ctx->dev_small + 0, ctx->dev_small + 2);
+  st = build_chunks(ctx, act_scan, ctx->chunks, ctx->dev_small + 0, ctx->dev_small + 2);
   if (st != P3M_OK) return st;
   ctx->pairs_built = true;
   return P3M_OK;
@@ -1837,7 +1811,6 @@ extern "C" p3m_status p3m_sr_forces(p3m_sr_ctx* ctx, const double* pos, int prec
   TraversalArgs a = base_args(ctx);
   a.pos = pos;
   a.chunks = ctx->chunks;
-  a.order = ctx->order;
   a.n_chunks = ctx->dev_small + 0;
   a.counter = ctx->dev_small + 3;
   a.active_idx = ctx->all_active ? nullptr : ctx->active_idx;
@@ -1916,7 +1889,6 @@ extern "C" p3m_status p3m_sr_forces_tabulated(p3m_sr_ctx* ctx, const double* pos
   TraversalArgs a = base_args(ctx);
   a.pos = pos;
   a.chunks = ctx->chunks;
-  a.order = ctx->order;
   a.n_chunks = ctx->dev_small + 0;
   a.counter = ctx->dev_small + 3;
   a.active_idx = ctx->all_active ? nullptr : ctx->active_idx;
@@ -1987,7 +1959,6 @@ extern "C" p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precisi
   TraversalArgs a = base_args(ctx);
   a.pos = pos;
   a.chunks = ctx->chunks_all;
-  a.order = ctx->order_all;
   a.n_chunks = ctx->dev_small + 1;
   a.counter = ctx->dev_small + 4;
   a.active_idx = nullptr;
@@ -2204,12 +2175,11 @@ extern "C" p3m_status p3m_sr_forces_noalloc(const p3m_sr_params* params, void* c
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   // receiver chunks (all particles active)
   const int64_t nrows = (int64_t)g.n_t * g.n_t * ((g.n_t + kChunkSpan - 1) / kChunkSpan);  // segments
-  k_row_chunks<<<(unsigned)((nrows + 1 + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows, nullptr,
-                                                                   nullptr);
+  k_row_chunks<<<(unsigned)((nrows + 1 + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   if (!ok(scan_exclusive_i32(rows, rows, nrows + 1, scan, kNoallocScanInts, s, &launches))) return P3M_ERR_CUDA;
   k_write_chunks<<<(unsigned)((nrows + 127) / 128), 128, 0, s>>>(offsets, nullptr, g.n_t, g.nsub3, rows, chunks,
-                                                                 small + 0, nullptr, n, nullptr, nullptr, nullptr);
+                                                                 small + 0, nullptr, n);
   if (!ok(cudaGetLastError())) return P3M_ERR_CUDA;
   // pair forces in the sorted order, then back to the caller's order
   static SeriesConsts series = make_series();

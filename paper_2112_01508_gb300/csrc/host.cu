@@ -379,10 +379,6 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
   P3M_ALLOC(ctx->act_scan, n + 1);
   P3M_ALLOC(ctx->active_idx, n);
   P3M_ALLOC(ctx->tile_chunks, ctx->n_tiles + 1);
-  P3M_ALLOC(ctx->seg_bucket, ctx->n_tiles + 1);
-  P3M_ALLOC(ctx->bucket_cursor, kCostBuckets);
-  P3M_ALLOC(ctx->order, ctx->max_chunks);
-  P3M_ALLOC(ctx->order_all, ctx->max_chunks);
   P3M_ALLOC(ctx->part_acc, std::min<int64_t>(kPartItems, ctx->max_chunks * kMaxParts) * kChunk);
   P3M_ALLOC(ctx->chunks, ctx->max_chunks);
   P3M_ALLOC(ctx->chunks_all, ctx->max_chunks);
@@ -499,7 +495,7 @@ extern "C" void p3m_sr_destroy(p3m_sr_ctx* ctx) {
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
   void* ptrs[] = {ctx->keys[0], ctx->keys[1], ctx->vals[0], ctx->vals[1], ctx->offsets, ctx->hist,
                   ctx->scan_scratch, ctx->gather_tmp, ctx->active_flag, ctx->act_scan, ctx->active_idx,
-                  ctx->tile_chunks, ctx->seg_bucket, ctx->bucket_cursor, ctx->order, ctx->order_all, ctx->part_acc,
+                  ctx->tile_chunks, ctx->part_acc,
                   ctx->chunks, ctx->chunks_all, ctx->dev_small, ctx->pair_count,
                   ctx->rel4, ctx->abar4, ctx->abar_d, ctx->table, ctx->err_dev, ctx->drift_slots};
   for (void* p : ptrs)
