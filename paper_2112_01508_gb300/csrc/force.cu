@@ -44,10 +44,13 @@ namespace p3m {
 
 constexpr int kForceThreads = 128;
 constexpr int kForceWarps = kForceThreads / kWarp;
+// Supplier subtiles buffered per warp before their particles are walked: 256
+// measured best on the 128^3 and 512^3 sets (the one-sided kernel 4-8% faster than
+// with 128, the each-pair-once kernel unchanged; 64 slower).
 #ifndef P3M_LISTCAP
-#define P3M_LISTCAP 128
+#define P3M_LISTCAP 256
 #endif
-constexpr int kListCap = P3M_LISTCAP;  // supplier subtiles buffered per warp
+constexpr int kListCap = P3M_LISTCAP;
 
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -758,10 +761,11 @@ struct PackedSmem {
 #endif
 };
 
-// 6 resident blocks of 4 warps per SM bound the kernel to ~80 registers;
-// measured best among 1, 6 and 8 on the 128^3 set.
+// 7 resident blocks of 4 warps per SM bound the kernel to 70 registers (no
+// spills); with the cp.async staging measured best among 5 to 8 on the state of the
+// 128^3 set after 25 benchmark steps (deep-rung substep 3% faster than with 6).
 #ifndef P3M_GP_MINBLOCKS
-#define P3M_GP_MINBLOCKS 6
+#define P3M_GP_MINBLOCKS 7
 #endif
 
 template <int SOFT, bool TABLE = false>
