@@ -343,6 +343,7 @@ struct ChunkFrame {
   Vec3<Real> pi;    // receiver position (chunk frame in FP32, absolute in FP64)
   Vec3<Real> lo, hi;  // bounding box of the receivers
   int elo[3], ext[3];  // candidate subtile block (offsets from g0) and its extent
+  float inv_ext[2];    // 1 / ext[2], 1 / ext[1], for decoding candidate indices
   Real org[3];      // position of g0's origin in the frame
 };
 
@@ -399,7 +400,13 @@ __device__ __forceinline__ void load_chunk(const TraversalArgs& a, const Reach& 
     if constexpr (sizeof(Real) == 4) F.org[d] = 0.0f;
     else F.org[d] = (double)F.g0[d] * g.side64[d];
   }
+  F.inv_ext[0] = 1.0f / (float)F.ext[2];
+  F.inv_ext[1] = 1.0f / (float)F.ext[1];
 }
+
+#ifndef P3M_FAST_DECODE
+#define P3M_FAST_DECODE 1  // candidate decoding and subtile encoding without integer division
+#endif
 
 // Candidate subtile cc (of ncand) of the blocky ball around the chunk's subtile
 // block: whether its box gap to the receivers' bounding box is below the reach
@@ -414,10 +421,16 @@ __device__ __forceinline__ bool candidate_range(const TraversalArgs& a, const Re
   cnt = 0;
   dpk = 0;
   if (cc >= ncand) return false;
-  int dz = cc % F.ext[2];
-  int t = cc / F.ext[2];
-  int dy = t % F.ext[1];
-  int dx = t / F.ext[1];
+  int t, dx;
+  if (P3M_FAST_DECODE && ncand < (1 << 22)) {  // always, unless a drift has widened the block enormously
+    t = quot_small(cc, F.ext[2], F.inv_ext[0]);
+    dx = quot_small(t, F.ext[1], F.inv_ext[1]);
+  } else {
+    t = cc / F.ext[2];
+    dx = t / F.ext[1];
+  }
+  int dz = cc - t * F.ext[2];
+  int dy = t - dx * F.ext[1];
   dx += F.elo[0]; dy += F.elo[1]; dz += F.elo[2];
   const int dd[3] = {dx, dy, dz};
   const Real blo[3] = {F.lo.x, F.lo.y, F.lo.z}, bhi[3] = {F.hi.x, F.hi.y, F.hi.z};
@@ -438,7 +451,7 @@ __device__ __forceinline__ bool candidate_range(const TraversalArgs& a, const Re
   gx += gx < 0 ? g.M[0] : (gx >= g.M[0] ? -g.M[0] : 0);
   gy += gy < 0 ? g.M[1] : (gy >= g.M[1] ? -g.M[1] : 0);
   gz += gz < 0 ? g.M[2] : (gz >= g.M[2] ? -g.M[2] : 0);
-  const int sid = encode_subtile(g, gx, gy, gz);
+  const int sid = P3M_FAST_DECODE ? encode_subtile_fast(g, gx, gy, gz) : encode_subtile(g, gx, gy, gz);
   start = max(a.offsets[sid], clip_from);
   cnt = a.offsets[sid + 1] - start;
   dpk = pack_delta(dx, dy, dz);

@@ -262,6 +262,7 @@ void setup_geometry(p3m_sr_ctx* ctx) {
     g.side64[d] = p.box / (double)g.M[d];
     g.side32[d] = (float)g.side64[d];
     g.R[d] = (int)std::ceil(p.x_r / g.side64[d] * (1.0 + 1e-12));
+    g.inv_ns[d] = 1.0f / (float)g.ns[d];
   }
   ctx->n_tiles = (int64_t)g.n_t * g.n_t * g.n_t;
 }
