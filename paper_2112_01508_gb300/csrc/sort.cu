@@ -114,7 +114,9 @@ __global__ void k_radix_hist(const int* __restrict__ keys, int64_t n, int shift,
 
 // Stable scatter of one radix pass.  Warp w of a block owns the contiguous
 // items [w*512, (w+1)*512) of the block's tile and walks them in 16 steps of
-// 32 consecutive items, so ranks follow the input order.
+// 32 consecutive items, so ranks follow the input order.  The block then puts
+// its tile in digit order in shared memory and writes it out from there, so that
+// consecutive threads write consecutive positions of each digit's run.
 // hist_next (nullable, zeroed before the launch): the digit counts of the next pass
 // (bits_next bits from shift_next) per output tile, accumulated here with one atomic
 // per distinct (digit, tile) of each warp, so that pass needs no histogram kernel.
@@ -122,13 +124,17 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
     const int* __restrict__ keys_in, const int* __restrict__ vals_in, int* __restrict__ keys_out,
     int* __restrict__ vals_out, int64_t n, int shift, int bits, const int* __restrict__ hist, int nblocks,
     int* __restrict__ hist_next, int shift_next, int bits_next) {
-  __shared__ int wcnt[kRadixWarps][kMaxRadix];
+  __shared__ int wcnt[kRadixWarps][kMaxRadix];  // per-warp digit counts; later the staged tile
+  __shared__ int bstart[kMaxRadix];             // first position of each digit in the block's tile
+  __shared__ int wtot[kRadixWarps];
+  static_assert(kRadixWarps * kMaxRadix >= 2 * kRadixTile, "staging area");
   const int radix = 1 << bits;
   const int mask = radix - 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = lane; d < radix; d += 32) wcnt[warp][d] = 0;
   __syncwarp();
-  const int64_t wbase = (int64_t)blockIdx.x * kRadixTile + (int64_t)warp * (kRadixSteps * kWarp);
+  const int64_t tile0 = (int64_t)blockIdx.x * kRadixTile;
+  const int64_t wbase = tile0 + (int64_t)warp * (kRadixSteps * kWarp);
   const unsigned lt = (1u << lane) - 1u;
   int key[kRadixSteps], val[kRadixSteps], rank[kRadixSteps];
 #pragma unroll
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
     rank[k] = base + r;
   }
   __syncthreads();
-  // exclusive prefix over the warps of the block, per digit
+  // exclusive prefix over the warps of the block, per digit; the digit totals
   for (int d = threadIdx.x; d < radix; d += blockDim.x) {
     int run = 0;
 #pragma unroll
@@ -157,20 +163,65 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
       wcnt[w][d] = run;
       run += t;
     }
+    bstart[d] = run;
+  }
+  __syncthreads();
+  // exclusive scan of the digit totals: thread t holds digits [4t, 4t + 4)
+  {
+    int v[4], tot = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int d = 4 * threadIdx.x + q;
+      v[q] = d < radix ? bstart[d] : 0;
+      tot += v[q];
+    }
+    int inc = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane == 31) wtot[warp] = inc;
+    __syncthreads();
+    int run = inc - tot;
+    for (int w = 0; w < warp; ++w) run += wtot[w];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int d = 4 * threadIdx.x + q;
+      if (d < radix) bstart[d] = run;
+      run += v[q];
+    }
+  }
+  __syncthreads();
+  int lp[kRadixSteps];  // position of each item in the block's digit-ordered tile
+#pragma unroll
+  for (int k = 0; k < kRadixSteps; ++k) {
+    const int d = (key[k] >> shift) & mask;
+    lp[k] = bstart[d] + wcnt[warp][d] + rank[k];
+  }
+  __syncthreads();  // every warp has read wcnt
+  int* sk = &wcnt[0][0];
+  int* sv = sk + kRadixTile;
+  const int64_t left = n - tile0;
+  const int nvalid = left < kRadixTile ? (int)left : kRadixTile;
+#pragma unroll
+  for (int k = 0; k < kRadixSteps; ++k) {
+    if (wbase + k * kWarp + lane < n) {
+      sk[lp[k]] = key[k];
+      sv[lp[k]] = val[k];
+    }
   }
   __syncthreads();
   const int mask_next = (1 << bits_next) - 1;
-#pragma unroll
-  for (int k = 0; k < kRadixSteps; ++k) {
-    int64_t i = wbase + k * kWarp + lane;
-    const bool valid = i < n;
+  for (int p = threadIdx.x; p < kRadixTile; p += kRadixThreads) {
+    const bool valid = p < nvalid;
     int tag = -1 - lane;
     if (valid) {
-      int d = (key[k] >> shift) & mask;
-      int64_t dst = (int64_t)hist[(int64_t)d * nblocks + blockIdx.x] + wcnt[warp][d] + rank[k];
-      keys_out[dst] = key[k];
-      vals_out[dst] = val[k];
-      tag = ((key[k] >> shift_next) & mask_next) * nblocks + (int)(dst / kRadixTile);
+      const int kk = sk[p];
+      const int d = (kk >> shift) & mask;
+      const int64_t dst = (int64_t)hist[(int64_t)d * nblocks + blockIdx.x] + (p - bstart[d]);
+      keys_out[dst] = kk;
+      vals_out[dst] = sv[p];
+      tag = ((kk >> shift_next) & mask_next) * nblocks + (int)(dst / kRadixTile);
     }
     if (hist_next) {  // uniform over the launch
       const unsigned peers = __match_any_sync(0xffffffffu, tag);
