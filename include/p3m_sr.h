@@ -398,7 +398,7 @@ p3m_status p3m_sr_vjp(p3m_sr_ctx* ctx, const double* pos, int precision, const v
  * receiver chunks and evaluates the FP32 forces with the same kernels as
  * p3m_sr_sort + p3m_sr_build_pairs + p3m_sr_forces (all particles active), but
  * keeps every intermediate array in one fixed-size device array inside the
- * library (about 7.6 MB, held by every GPU that loads the library until the
+ * library (about 7.9 MB, held by every GPU that loads the library until the
  * process exits).
  *   params      as for p3m_sr_create; n <= 65536, at most 2^18 subtiles and
  *               2^14 chunk segments (n_t^2 ceil(n_t/4)), x_r <= 4.6 x_s.  Larger inputs return

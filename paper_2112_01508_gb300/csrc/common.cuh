@@ -36,6 +36,9 @@ struct Geometry {
   float inv_ns[3];    // 1 / ns[d], for quotients of small integers (see quot_small)
   double side64[3];   // L / M[d]
   float side32[3];    // (float) side64
+  // multipliers of quot_magic for nsub3, n_t^2, n_t, ns[1] ns[2] and ns[2]
+  unsigned long long mg_nsub3, mg_nt2, mg_nt, mg_s12, mg_s2;
+  const double* org = nullptr;  // device table of subtile origins i * side64[d]: x at [0, M[0]), then y, then z
 };
 
 // Constants of the pair force (Eq. p3m_gravity, short-range bracket).
@@ -69,19 +72,28 @@ struct Chunk {
 
 // ---- small device helpers -------------------------------------------------
 
+// floor(a / d) for 0 <= a < 2^31 and 1 <= d < 2^33 from m = magic_u64(d): the high
+// word of a * m (division by an invariant integer through multiplication,
+// Granlund and Montgomery 1994).  With m = ceil(2^64 / d) the product overshoots
+// a / d by less than a 2^-64 < 1 / d, which never reaches the next integer; d = 1
+// has no 64-bit multiplier and is passed through.
+__device__ __forceinline__ int quot_magic(int a, int d, unsigned long long m) {
+  return d == 1 ? a : (int)__umul64hi((unsigned long long)a, m);
+}
+
 __device__ __forceinline__ void decode_subtile(const Geometry& g, int id, int& gx, int& gy, int& gz) {
-  int tile = id / g.nsub3;
-  int sub = id - tile * g.nsub3;
-  int nt2 = g.n_t * g.n_t;
-  int tx = tile / nt2;
-  int rem = tile - tx * nt2;
-  int ty = rem / g.n_t;
-  int tz = rem - ty * g.n_t;
-  int s12 = g.ns[1] * g.ns[2];
-  int sx = sub / s12;
-  int srem = sub - sx * s12;
-  int sy = srem / g.ns[2];
-  int sz = srem - sy * g.ns[2];
+  const int tile = quot_magic(id, g.nsub3, g.mg_nsub3);
+  const int sub = id - tile * g.nsub3;
+  const int nt2 = g.n_t * g.n_t;
+  const int tx = quot_magic(tile, nt2, g.mg_nt2);
+  const int rem = tile - tx * nt2;
+  const int ty = quot_magic(rem, g.n_t, g.mg_nt);
+  const int tz = rem - ty * g.n_t;
+  const int s12 = g.ns[1] * g.ns[2];
+  const int sx = quot_magic(sub, s12, g.mg_s12);
+  const int srem = sub - sx * s12;
+  const int sy = quot_magic(srem, g.ns[2], g.mg_s2);
+  const int sz = srem - sy * g.ns[2];
   gx = tx * g.ns[0] + sx;
   gy = ty * g.ns[1] + sy;
   gz = tz * g.ns[2] + sz;
@@ -115,9 +127,27 @@ __device__ __forceinline__ int encode_subtile(const Geometry& g, int gx, int gy,
   return tile * g.nsub3 + (sx * g.ns[1] + sy) * g.ns[2] + sz;
 }
 
+// FP32 coordinates of (x, y, z) relative to the origin of subtile (gx, gy, gz):
+// per axis one FP64 subtraction of the tabulated origin (g.org) and one
+// conversion.  On this part the FP64 pipe is the scarce resource of every
+// per-particle pass, so the origin is read, not computed, and no FP64 comparison
+// is made.
+__device__ __forceinline__ void rel_to_subtile(const Geometry& g, double x, double y, double z, int gx, int gy,
+                                               int gz, double r[3]) {
+  r[0] = __dsub_rn(x, __ldg(g.org + gx));
+  r[1] = __dsub_rn(y, __ldg(g.org + g.M[0] + gy));
+  r[2] = __dsub_rn(z, __ldg(g.org + g.M[0] + g.M[1] + gz));
+}
+
+// Subtile origins i * side64[d] for the table g.org (M[0] + M[1] + M[2] entries).
+__global__ void k_fill_origins(Geometry g, double* __restrict__ org);
+
 // ---- kernels of sort.cu launched from other translation units ---------------
 constexpr int kRadixThreadsPublic = 256;
-constexpr int kRadixTilePublic = 4096;  // items per radix block
+#ifndef P3M_RADIX_STEPS
+#define P3M_RADIX_STEPS 8  // radix items per lane (8: 2048-item tiles, 7% faster than 4096 at 128^3, 26% at 512^3)
+#endif
+constexpr int kRadixTilePublic = kRadixThreadsPublic * P3M_RADIX_STEPS;  // items per radix block
 __global__ void k_bin(const double* __restrict__ pos, int64_t n, Geometry g, int* __restrict__ keys,
                       int* __restrict__ vals, int* __restrict__ counts, int* __restrict__ err);
 __global__ void k_radix_hist(const int* __restrict__ keys, int64_t n, int shift, int bits, int* __restrict__ hist,

@@ -46,6 +46,8 @@ struct p3m_sr_ctx {
 
   // ---- per-call arrays ----
   float4* rel4 = nullptr;             // FP32 subtile-relative coordinates (+ id bits)
+  double* org = nullptr;              // subtile origins per axis (geo.org points here)
+  int64_t org_cap = 0;                // allocated doubles of org
   float4* abar4 = nullptr;            // vjp: masked abar, FP32
   double* abar_d = nullptr;           // vjp: masked abar, FP64 (3 n)
   float* table = nullptr;             // tabulated bracket (p3m_sr_forces_tabulated)

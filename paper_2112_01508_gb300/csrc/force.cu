@@ -59,23 +59,38 @@ static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // ---------------------------------------------------------------------------
 
 // FP32 coordinates relative to the particle's subtile origin, plus the id bits.
+// All lanes of a warp reach the vote: launched with whole warps, lanes past n only vote.
 __global__ void k_rel4(const double* __restrict__ pos, const int* __restrict__ cell, int64_t n, Geometry g,
                        float4* __restrict__ rel4) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int id = cell[i];
-  int gx, gy, gz;
-  decode_subtile(g, id, gx, gy, gz);
-  // relative to the origin of the subtile of the last sort; a particle that
-  // drifted across the periodic boundary since then takes its nearest image
-  double r[3] = {__fma_rn(-(double)gx, g.side64[0], pos[i]), __fma_rn(-(double)gy, g.side64[1], pos[n + i]),
-                 __fma_rn(-(double)gz, g.side64[2], pos[2 * n + i])};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    if (r[d] > 0.5 * g.box) r[d] -= g.box;
-    else if (r[d] < -0.5 * g.box) r[d] += g.box;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < n;
+  int id = 0, gx = 0, gy = 0, gz = 0;
+  double x = 0.0, y = 0.0, z = 0.0;
+  if (valid) {
+    id = cell[i];
+    decode_subtile(g, id, gx, gy, gz);
+    x = pos[i];
+    y = pos[n + i];
+    z = pos[2 * n + i];
   }
-  rel4[i] = make_float4((float)r[0], (float)r[1], (float)r[2], __int_as_float(id));
+  double r[3];
+  rel_to_subtile(g, x, y, z, gx, gy, gz, r);
+  float f[3] = {(float)r[0], (float)r[1], (float)r[2]};
+  // relative to the origin of the subtile of the last sort; a particle that drifted
+  // across the periodic boundary since then takes its nearest image.  Its offset is
+  // then near +-L, every other one far below L/2, so the test is made in FP32, and
+  // only warps that hold such a particle spend FP64 operations on it.
+  const float half = 0.5f * (float)g.box;
+  const bool far = fabsf(f[0]) > half || fabsf(f[1]) > half || fabsf(f[2]) > half;
+  if (__any_sync(0xffffffffu, far)) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (fabsf(f[d]) > half) {
+        r[d] = f[d] > 0.0f ? __dsub_rn(r[d], g.box) : __dadd_rn(r[d], g.box);
+        f[d] = (float)r[d];
+      }
+  }
+  if (valid) rel4[i] = make_float4(f[0], f[1], f[2], __int_as_float(id));
 }
 
 // The receiver set in two passes over tiles of kActTile sorted particles: the number
@@ -777,6 +792,10 @@ struct PackedSmem {
 // 7 resident blocks of 4 warps per SM bound the kernel to 70 registers (no
 // spills); with the cp.async staging measured best among 5 to 8 on the state of the
 // 128^3 set after 25 benchmark steps (deep-rung substep 3% faster than with 6).
+#ifndef P3M_GP_UNROLL
+#define P3M_GP_UNROLL 2  // supplier pairs per loop iteration (2: 2-3% faster than 1 on the 128^3 set)
+#endif
+constexpr int kGpUnroll = P3M_GP_UNROLL;
 #ifndef P3M_GP_MINBLOCKS
 #define P3M_GP_MINBLOCKS 7
 #endif
@@ -894,6 +913,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
         // without the softened-branch test (a vote and a branch per step).
         auto run_pairs = [&](auto check_soft) {
           constexpr bool kCheckSoft = decltype(check_soft)::value;
+#pragma unroll kGpUnroll
         for (int p = 0; p < npairs; ++p) {
           const float4 s = S.sxy[p];
           const float2 z = S.sz[p];
@@ -1045,6 +1065,10 @@ struct SymVjpSmem : SymSmem {
 // 5 resident blocks of 4 warps per SM (96 registers, a few bytes of spills): with the
 // cp.async staging measured best on the 128^3 set (1.490 ms against 1.518 with 4
 // blocks and 128 registers).
+#ifndef P3M_SYM_UNROLL
+#define P3M_SYM_UNROLL 1  // rotation steps per loop iteration
+#endif
+constexpr int kSymUnroll = P3M_SYM_UNROLL;
 #ifndef P3M_SYM_MINBLOCKS
 #define P3M_SYM_MINBLOCKS 5
 #endif
@@ -1202,6 +1226,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
       auto run = [&](auto check_soft, auto masked) {
         constexpr bool kCheckSoft = decltype(check_soft)::value;
         constexpr bool kMasked = decltype(masked)::value;
+#pragma unroll kSymUnroll
         for (int k = 0; k < P; ++k) {
           const float4 s = S.sxy[q];
           const float2 z = S.sz[q];
@@ -1554,6 +1579,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_vjp_packed(Trav
         // receivers' box skip the softened-branch test
         auto run_pairs = [&](auto check_soft) {
           constexpr bool kCheckSoft = decltype(check_soft)::value;
+#pragma unroll kGpUnroll
         for (int p = 0; p < npairs; ++p) {
           const float4 s = S.sxy[p];
           const float2 z = S.sz[p];

@@ -246,6 +246,11 @@ p3m_status validate_params(p3m_sr_ctx* ctx, const p3m_sr_params& p) {
   return P3M_OK;
 }
 
+// ceil(2^64 / d) for d >= 2 (0 for d = 1, which quot_magic passes through).
+static unsigned long long magic_u64(int64_t d) {
+  return d <= 1 ? 0ULL : ~0ULL / (unsigned long long)d + 1ULL;
+}
+
 void setup_geometry(p3m_sr_ctx* ctx) {
   const p3m_sr_params& p = ctx->prm;
   Geometry& g = ctx->geo;
@@ -265,6 +270,23 @@ void setup_geometry(p3m_sr_ctx* ctx) {
     g.inv_ns[d] = 1.0f / (float)g.ns[d];
   }
   ctx->n_tiles = (int64_t)g.n_t * g.n_t * g.n_t;
+  g.mg_nsub3 = magic_u64(g.nsub3);
+  g.mg_nt2 = magic_u64((int64_t)g.n_t * g.n_t);
+  g.mg_nt = magic_u64(g.n_t);
+  g.mg_s12 = magic_u64((int64_t)g.ns[1] * g.ns[2]);
+  g.mg_s2 = magic_u64(g.ns[2]);
+}
+
+static int64_t origin_count(const Geometry& g) { return (int64_t)g.M[0] + g.M[1] + g.M[2]; }
+
+// Fill the subtile-origin table of the current geometry (stream-ordered: work
+// queued before still reads the previous values).
+static p3m_status fill_origins(p3m_sr_ctx* ctx) {
+  ctx->geo.org = ctx->org;
+  const int64_t m = origin_count(ctx->geo);
+  k_fill_origins<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(ctx->geo, ctx->org);
+  ++ctx->launches;
+  return cuda_check(ctx, cudaGetLastError(), "origin table kernel");
 }
 
 void setup_force_consts(p3m_sr_ctx* ctx) {
@@ -356,7 +378,7 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
   const int64_t n = ctx->n;
   const int64_t S = ctx->geo.S;
   setup_radix(ctx);
-  int64_t radix_blocks = (n + 4095) / 4096;
+  int64_t radix_blocks = (n + kRadixTilePublic - 1) / kRadixTilePublic;
   ctx->hist_ints = 1024 * (radix_blocks > 0 ? radix_blocks : 1);
   ctx->scan_scratch_ints = scan_scratch_ints(scan_length(ctx));
   ctx->offsets_cap = S + 1;
@@ -386,6 +408,8 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
   P3M_ALLOC(ctx->dev_small, 16);
   P3M_ALLOC(ctx->pair_count, 2);
   P3M_ALLOC(ctx->rel4, n);
+  P3M_ALLOC(ctx->org, origin_count(ctx->geo));
+  ctx->org_cap = origin_count(ctx->geo);
   P3M_ALLOC(ctx->err_dev, 1);
   P3M_ALLOC(ctx->drift_slots, kMaxDrifts);
 #undef P3M_ALLOC
@@ -416,6 +440,7 @@ extern "C" p3m_status p3m_sr_create(const p3m_sr_params* params, void* cuda_stre
   if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->pair_count, 0, 2 * sizeof(unsigned long long), ctx->stream),
                        "memset")) != P3M_OK)
     goto fail_alloc;
+  if ((st = fill_origins(ctx)) != P3M_OK) goto fail_alloc;
   *out = ctx;
   return P3M_OK;
 fail_alloc:
@@ -462,10 +487,22 @@ extern "C" p3m_status p3m_sr_set_subtiles(p3m_sr_ctx* ctx, const int* n_sub) {
   int64_t scan_ints = scan_scratch_ints(scan_length(ctx));
   int* new_offsets = nullptr;
   int* new_scan = nullptr;
+  double* new_org = nullptr;
+  const int64_t n_org = origin_count(ctx->geo);
   if (S + 1 > ctx->offsets_cap && (st = alloc(ctx, &new_offsets, S + 1, "offsets")) != P3M_OK) goto restore;
   if (scan_ints > ctx->scan_scratch_ints && (st = alloc(ctx, &new_scan, scan_ints, "scan_scratch")) != P3M_OK) {
     cudaFree(new_offsets);
     goto restore;
+  }
+  if (n_org > ctx->org_cap && (st = alloc(ctx, &new_org, n_org, "org")) != P3M_OK) {
+    cudaFree(new_offsets);
+    cudaFree(new_scan);
+    goto restore;
+  }
+  if (new_org) {
+    cudaFree(ctx->org);
+    ctx->org = new_org;
+    ctx->org_cap = n_org;
   }
   if (new_offsets) {
     cudaFree(ctx->offsets);
@@ -479,6 +516,7 @@ extern "C" p3m_status p3m_sr_set_subtiles(p3m_sr_ctx* ctx, const int* n_sub) {
     if ((st = cuda_check(ctx, cudaMemsetAsync(new_scan, 0, sizeof(int) * scan_ints, ctx->stream), "memset")) != P3M_OK)
       return st;
   }
+  if ((st = fill_origins(ctx)) != P3M_OK) return st;
   setup_radix(ctx);
   ctx->sorted = false;
   ctx->sorted_pos = nullptr;
@@ -498,7 +536,7 @@ extern "C" void p3m_sr_destroy(p3m_sr_ctx* ctx) {
                   ctx->scan_scratch, ctx->gather_tmp, ctx->active_flag, ctx->act_scan, ctx->active_idx,
                   ctx->tile_chunks, ctx->part_acc,
                   ctx->chunks, ctx->chunks_all, ctx->dev_small, ctx->pair_count,
-                  ctx->rel4, ctx->abar4, ctx->abar_d, ctx->table, ctx->err_dev, ctx->drift_slots};
+                  ctx->rel4, ctx->org, ctx->abar4, ctx->abar_d, ctx->table, ctx->err_dev, ctx->drift_slots};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->err_host) cudaFreeHost(ctx->err_host);

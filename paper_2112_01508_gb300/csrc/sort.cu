@@ -16,8 +16,8 @@ namespace p3m {
 
 constexpr int kRadixThreads = 256;
 constexpr int kRadixWarps = kRadixThreads / kWarp;
-constexpr int kRadixSteps = 16;                           // items per lane
-constexpr int kRadixTile = kRadixThreads * kRadixSteps;   // 4096 items per block
+constexpr int kRadixSteps = P3M_RADIX_STEPS;              // items per lane
+constexpr int kRadixTile = kRadixThreads * kRadixSteps;   // items per block
 static_assert(kRadixThreads == kRadixThreadsPublic && kRadixTile == kRadixTilePublic, "radix tiling");
 
 // Subtile id of particle i: g_d = min(floor(x_d M_d / L), M_d - 1) with one correctly
@@ -42,7 +42,7 @@ __device__ __forceinline__ int bin_one(const double* __restrict__ pos, int64_t n
     if (e >= 0) q = (int)((((pb & 0xfffffffffffffLL) | (1LL << 52)) >> (52 - e)));
     gc[d] = q < g.M[d] - 1 ? q : g.M[d] - 1;
   }
-  return encode_subtile(g, gc[0], gc[1], gc[2]);
+  return encode_subtile_fast(g, gc[0], gc[1], gc[2]);  // 0 <= gc < M < 2^22
 }
 
 __global__ void k_bin(const double* __restrict__ pos, int64_t n, Geometry g, int* __restrict__ keys,
@@ -255,8 +255,9 @@ __global__ void k_gather_pos_rel4(const double* __restrict__ src, const int* __r
   const int id = cell[k];
   int gx, gy, gz;
   decode_subtile(g, id, gx, gy, gz);
-  rel4[k] = make_float4((float)__fma_rn(-(double)gx, g.side64[0], x), (float)__fma_rn(-(double)gy, g.side64[1], y),
-                        (float)__fma_rn(-(double)gz, g.side64[2], z), __int_as_float(id));
+  double r[3];
+  rel_to_subtile(g, x, y, z, gx, gy, gz, r);
+  rel4[k] = make_float4((float)r[0], (float)r[1], (float)r[2], __int_as_float(id));
 }
 
 // Carried arrays of an out-of-place sort: element bytes as `words` words of
@@ -292,8 +293,9 @@ __global__ void k_gather_all(const double* __restrict__ src, const int* __restri
   const int id = cell[k];
   int gx, gy, gz;
   decode_subtile(g, id, gx, gy, gz);
-  rel4[k] = make_float4((float)__fma_rn(-(double)gx, g.side64[0], x), (float)__fma_rn(-(double)gy, g.side64[1], y),
-                        (float)__fma_rn(-(double)gz, g.side64[2], z), __int_as_float(id));
+  double r[3];
+  rel_to_subtile(g, x, y, z, gx, gy, gz, r);
+  rel4[k] = make_float4((float)r[0], (float)r[1], (float)r[2], __int_as_float(id));
   for (int c = 0; c < cs.count; ++c) {
     switch (cs.wbytes[c]) {
       case 8: copy_words<unsigned long long>(cs.src[c], cs.dst[c], j, k, cs.words[c]); break;
@@ -311,6 +313,14 @@ __global__ void k_gather_words(const T* __restrict__ src, const int* __restrict_
   if (k >= n) return;
   int64_t j = perm[k];
   for (int w = 0; w < words; ++w) dst[k * words + w] = src[j * words + w];
+}
+
+__global__ void k_fill_origins(Geometry g, double* __restrict__ org) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int d = i < g.M[0] ? 0 : (i < g.M[0] + g.M[1] ? 1 : 2);
+  const int j = i - (d > 0 ? g.M[0] : 0) - (d > 1 ? g.M[1] : 0);
+  if (d == 2 && j >= g.M[2]) return;
+  org[i] = __dmul_rn((double)j, g.side64[d]);
 }
 
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
