@@ -119,19 +119,34 @@ __global__ void __launch_bounds__(kActThreads) k_active_count(const int8_t* __re
   }
 }
 
+// flag and act_scan are 16-byte aligned (context arrays); rung is read as 16-byte
+// vectors when it is too.
 __global__ void __launch_bounds__(kActThreads) k_active_scan_compact(const int8_t* __restrict__ rung, int64_t n,
                                                                      int rung_min, const int* __restrict__ tile_base,
                                                                      int8_t* __restrict__ flag, int* __restrict__ act_scan,
                                                                      int* __restrict__ active_idx) {
+  static_assert(kActItems == 16, "one 16-byte vector of rungs and flags per thread");
   __shared__ int warp_tot[kActThreads / kWarp];
   const int64_t base = (int64_t)blockIdx.x * kActTile + (int64_t)threadIdx.x * kActItems;  // 16 consecutive items
+  const bool whole = base + kActItems <= n;
   int f[kActItems];
   int tot = 0;
+  if (whole && ((reinterpret_cast<uintptr_t>(rung) & 15) == 0)) {
+    const int4 v = *reinterpret_cast<const int4*>(rung + base);
+    const int w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-  for (int k = 0; k < kActItems; ++k) {
-    const int64_t i = base + k;
-    f[k] = (i < n && rung[i] >= rung_min) ? 1 : 0;
-    tot += f[k];
+    for (int k = 0; k < kActItems; ++k) {
+      const int r = (int)(int8_t)((w[k >> 2] >> (8 * (k & 3))) & 0xff);
+      f[k] = r >= rung_min ? 1 : 0;
+      tot += f[k];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kActItems; ++k) {
+      const int64_t i = base + k;
+      f[k] = (i < n && rung[i] >= rung_min) ? 1 : 0;
+      tot += f[k];
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int inc = tot;
@@ -143,15 +158,31 @@ __global__ void __launch_bounds__(kActThreads) k_active_scan_compact(const int8_
   __syncthreads();
   int run = inc - tot + tile_base[blockIdx.x];
   for (int w = 0; w < warp; ++w) run += warp_tot[w];
+  if (whole) {  // vector stores: 16 flags, then 16 scan values as four int4
+    int fw[4] = {0, 0, 0, 0};
+    int sc[kActItems];
 #pragma unroll
-  for (int k = 0; k < kActItems; ++k) {
-    const int64_t i = base + k;
-    if (i <= n) act_scan[i] = run;
-    if (i < n) {
-      flag[i] = (int8_t)f[k];
-      if (f[k]) active_idx[run] = (int)i;
+    for (int k = 0; k < kActItems; ++k) {
+      fw[k >> 2] |= f[k] << (8 * (k & 3));
+      sc[k] = run;
+      if (f[k]) active_idx[run] = (int)(base + k);
+      run += f[k];
     }
-    run += f[k];
+    *reinterpret_cast<int4*>(flag + base) = make_int4(fw[0], fw[1], fw[2], fw[3]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      reinterpret_cast<int4*>(act_scan + base)[q] = make_int4(sc[4 * q], sc[4 * q + 1], sc[4 * q + 2], sc[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kActItems; ++k) {
+      const int64_t i = base + k;
+      if (i <= n) act_scan[i] = run;
+      if (i < n) {
+        flag[i] = (int8_t)f[k];
+        if (f[k]) active_idx[run] = (int)i;
+      }
+      run += f[k];
+    }
   }
 }
 
@@ -792,6 +823,9 @@ struct PackedSmem {
 // 7 resident blocks of 4 warps per SM bound the kernel to 70 registers (no
 // spills); with the cp.async staging measured best among 5 to 8 on the state of the
 // 128^3 set after 25 benchmark steps (deep-rung substep 3% faster than with 6).
+#ifndef P3M_GP_SOFT2
+#define P3M_GP_SOFT2 1  // close pairs of both halves in one packed softened evaluation
+#endif
 #ifndef P3M_GP_UNROLL
 #define P3M_GP_UNROLL 2  // supplier pairs per loop iteration (2: 2-3% faster than 1 on the 128^3 set)
 #endif
@@ -944,10 +978,16 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_force_packed(Tr
                 const bool rare0 = h0 && (q0 < a.f.rsw2_f) && (q0 > kR2Self);
                 const bool rare1 = h1 && (q1 < a.f.rsw2_f) && (q1 > kR2Self);
                 if (__any_sync(full, rare0 || rare1)) {
+#if P3M_GP_SOFT2
+                  float b0, b1, s0, s1;
+                  upk(B, b0, b1);
+                  upk(bracket_soft_f32x2<SOFT>(r2, a.f, a.sc), s0, s1);
+#else
                   float b0, b1, Ds;
                   upk(B, b0, b1);
                   const float s0 = bracket_soft_f32<SOFT, false>(q0, a.f, a.sc, Ds);
                   const float s1 = bracket_soft_f32<SOFT, false>(q1, a.f, a.sc, Ds);
+#endif
                   if (rare0) b0 = s0;
                   if (rare1) b1 = s1;
                   B = pk(b0, b1);
@@ -1065,6 +1105,9 @@ struct SymVjpSmem : SymSmem {
 // 5 resident blocks of 4 warps per SM (96 registers, a few bytes of spills): with the
 // cp.async staging measured best on the 128^3 set (1.490 ms against 1.518 with 4
 // blocks and 128 registers).
+#ifndef P3M_SYM_SOFT_INLINE
+#define P3M_SYM_SOFT_INLINE 1  // forward close pairs: 1 = packed softened form in the step (5-8% faster), 0 = queue
+#endif
 #ifndef P3M_SYM_UNROLL
 #define P3M_SYM_UNROLL 1  // rotation steps per loop iteration
 #endif
@@ -1256,6 +1299,14 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
             if (kCheckSoft && __any_sync(full, fminf(q0, q1) < a.f.rsw2_f)) {
               const bool rare0 = c0 > 0.f && q0 < a.f.rsw2_f && q0 > kR2Self;
               const bool rare1 = c1 > 0.f && q1 < a.f.rsw2_f && q1 > kR2Self;
+#if P3M_SYM_SOFT_INLINE
+              if (__any_sync(full, rare0 || rare1)) {  // both halves in one packed softened evaluation
+                float b0, b1, s0, s1;
+                upk(B, b0, b1);
+                upk(bracket_soft_f32x2<SOFT>(r2, a.f, a.sc), s0, s1);
+                B = pk(rare0 ? s0 : b0, rare1 ? s1 : b1);
+              }
+#else
               const unsigned rb0 = __ballot_sync(full, rare0), rb1 = __ballot_sync(full, rare1);
               if (rb0 | rb1) {
                 const int n0 = __popc(rb0);
@@ -1271,6 +1322,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
                   run_rare(nq, kWarp);
                 }
               }
+#endif
             }
             B = mul2(B, cm);
             ax = fma2(B, dx, ax);

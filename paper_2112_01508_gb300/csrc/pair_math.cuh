@@ -221,6 +221,51 @@ __device__ __forceinline__ float bracket_soft_f32(float r2, const ForceConsts& f
   return s3 - h * f.hscale_f;
 }
 
+// Softened branch for two pairs at once (forward only): both B-spline pieces are
+// evaluated and the piece of each half selected, so a warp whose close pairs sit
+// in either half pays one packed evaluation.  r comes from r^2 times its
+// reciprocal square root (r^2 > 0 here: a zero displacement never takes this
+// branch), and the outer piece's 1/x from the approximate reciprocal.  A half
+// that is not a close pair may overflow; the caller discards it.
+template <int SOFT>
+__device__ __forceinline__ f2 bracket_soft_f32x2(f2 r2, const ForceConsts& f, const SeriesConsts& sc) {
+  if (SOFT == P3M_SOFT_NONE) return pk(0.0f, 0.0f);
+  float a, b;
+  upk(r2, a, b);
+  const f2 r = mul2(r2, pk(rsqrt_approx(a), rsqrt_approx(b)));
+  const f2 u = mul2(r, pk(f.inv2xs_f, f.inv2xs_f));
+  const f2 u2 = mul2(u, u);
+  f2 h = pk(sc.h_f[kHTermsF - 1], sc.h_f[kHTermsF - 1]);
+#pragma unroll
+  for (int k = kHTermsF - 2; k >= 0; --k) h = fma2(h, u2, pk(sc.h_f[k], sc.h_f[k]));
+  f2 s3;
+  if (SOFT == P3M_SOFT_BSPLINE) {
+    const f2 x = mul2(r, pk(f.inv_epsb_f, f.inv_epsb_f));
+    const f2 x2 = mul2(x, x);
+    const f2 c = pk(f.bnorm_f, f.bnorm_f);
+    // x < 1/2: c (x^2 (x - 6/5) + 1/3)
+    const f2 s_in = mul2(c, fma2(x2, add2(x, pk(-1.2f, -1.2f)), pk(1.0f / 3.0f, 1.0f / 3.0f)));
+    // 1/2 <= x < 1: c (x^2 (6/5 - x/3) + 2/3 - 3x/2 - x^-3 / 480)
+    float xa, xb;
+    upk(x, xa, xb);
+    const f2 xi = pk(rcp_approx(xa), rcp_approx(xb));
+    const f2 xi3 = mul2(mul2(xi, xi), xi);
+    const f2 poly = fma2(x2, fma2(pk(-1.0f / 3.0f, -1.0f / 3.0f), x, pk(1.2f, 1.2f)),
+                         fma2(pk(-1.5f, -1.5f), x, pk(2.0f / 3.0f, 2.0f / 3.0f)));
+    const f2 s_out = mul2(c, fma2(xi3, pk(-1.0f / 480.0f, -1.0f / 480.0f), poly));
+    float ia, ib, oa, ob;
+    upk(s_in, ia, ib);
+    upk(s_out, oa, ob);
+    s3 = pk(xa < 0.5f ? ia : oa, xb < 0.5f ? ib : ob);
+  } else {  // Plummer
+    float pa, pb;
+    upk(add2(r2, pk(f.eps2_f, f.eps2_f)), pa, pb);
+    const f2 p = pk(rsqrt_approx(pa), rsqrt_approx(pb));
+    s3 = mul2(mul2(p, p), p);
+  }
+  return fma2(h, pk(-f.hscale_f, -f.hscale_f), s3);
+}
+
 // ---------------------------------------------------------------- FP64 ----
 
 template <int SOFT, bool VJP>
