@@ -1358,6 +1358,18 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
             if (kCheckSoft && __any_sync(full, fminf(q0, q1) < a.f.rsw2_f)) {
               const bool rare0 = c0 > 0.f && q0 < a.f.rsw2_f;
               const bool rare1 = c1 > 0.f && q1 < a.f.rsw2_f;
+#if P3M_SYM_SOFT_INLINE
+              if (__any_sync(full, rare0 || rare1)) {  // both halves in one packed softened evaluation
+                f2 Dsp;
+                float b0, b1, d0, d1, s0, s1, e0, e1;
+                upk(B, b0, b1);
+                upk(D, d0, d1);
+                upk(bracket_soft_vjp_f32x2<SOFT>(r2, a.f, a.sc, Dsp), s0, s1);
+                upk(Dsp, e0, e1);
+                B = pk(rare0 ? s0 : b0, rare1 ? s1 : b1);
+                D = pk(rare0 ? e0 : d0, rare1 ? e1 : d1);
+              }
+#else
               const unsigned rb0 = __ballot_sync(full, rare0), rb1 = __ballot_sync(full, rare1);
               if (rb0 | rb1) {
                 const int n0 = __popc(rb0);
@@ -1375,6 +1387,7 @@ __global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(Trav
                   run_rare(nq, kWarp);
                 }
               }
+#endif
             }
             if (kMasked) {  // selects: the receiver itself (r = 0) has non-finite main-branch values
               float b0, b1, d0, d1;
@@ -1659,9 +1672,16 @@ __global__ void __launch_bounds__(kPThreads, P3M_GP_MINBLOCKS) k_vjp_packed(Trav
             if (kCheckSoft) {
               const bool rare0 = h0 && (q0 < a.f.rsw2_f), rare1 = h1 && (q1 < a.f.rsw2_f);
               if (__any_sync(full, rare0 || rare1)) {
+#if P3M_GP_SOFT2
+                f2 Dsp;
+                float s0, s1, Ds0, Ds1;
+                upk(bracket_soft_vjp_f32x2<SOFT>(r2, a.f, a.sc, Dsp), s0, s1);
+                upk(Dsp, Ds0, Ds1);
+#else
                 float Ds0, Ds1;
                 const float s0 = bracket_soft_f32<SOFT, true>(q0, a.f, a.sc, Ds0);
                 const float s1 = bracket_soft_f32<SOFT, true>(q1, a.f, a.sc, Ds1);
+#endif
                 if (rare0) { b0 = s0; d0 = Ds0; }
                 if (rare1) { b1 = s1; d1 = Ds1; }
               }

@@ -266,6 +266,66 @@ __device__ __forceinline__ f2 bracket_soft_f32x2(f2 r2, const ForceConsts& f, co
   return fma2(h, pk(-f.hscale_f, -f.hscale_f), s3);
 }
 
+// Softened branch for two pairs at once with the derivative (adjoint): returns B
+// and sets D = B'(r)/r for both halves.  A zero displacement (coincident
+// particles) is allowed here and gives r = 0 (the inner piece's B(0) and D(0)).
+template <int SOFT>
+__device__ __forceinline__ f2 bracket_soft_vjp_f32x2(f2 r2, const ForceConsts& f, const SeriesConsts& sc, f2& D) {
+  if (SOFT == P3M_SOFT_NONE) {
+    D = pk(0.0f, 0.0f);
+    return pk(0.0f, 0.0f);
+  }
+  float a, b;
+  upk(r2, a, b);
+  const f2 r = pk(a > 0.0f ? a * rsqrt_approx(a) : 0.0f, b > 0.0f ? b * rsqrt_approx(b) : 0.0f);
+  const f2 u = mul2(r, pk(f.inv2xs_f, f.inv2xs_f));
+  const f2 u2 = mul2(u, u);
+  f2 h = pk(sc.h_f[kHTermsF - 1], sc.h_f[kHTermsF - 1]);
+  f2 hd = pk(sc.hd_f[kHTermsF - 1], sc.hd_f[kHTermsF - 1]);
+#pragma unroll
+  for (int k = kHTermsF - 2; k >= 0; --k) {
+    h = fma2(h, u2, pk(sc.h_f[k], sc.h_f[k]));
+    hd = fma2(hd, u2, pk(sc.hd_f[k], sc.hd_f[k]));
+  }
+  f2 s3, ds;
+  if (SOFT == P3M_SOFT_BSPLINE) {
+    const f2 x = mul2(r, pk(f.inv_epsb_f, f.inv_epsb_f));
+    const f2 x2 = mul2(x, x);
+    const float ce = f.bnorm_f * f.inv_epsb_f * f.inv_epsb_f;  // 32 / eps_B^5
+    const f2 c = pk(f.bnorm_f, f.bnorm_f), cc = pk(ce, ce);
+    const f2 s_in = mul2(c, fma2(x2, add2(x, pk(-1.2f, -1.2f)), pk(1.0f / 3.0f, 1.0f / 3.0f)));
+    const f2 d_in = mul2(cc, fma2(pk(3.0f, 3.0f), x, pk(-2.4f, -2.4f)));
+    float xa, xb;
+    upk(x, xa, xb);
+    const f2 xi = pk(rcp_approx(xa), rcp_approx(xb));
+    const f2 xi2 = mul2(xi, xi);
+    const f2 xi3 = mul2(xi2, xi);
+    const f2 poly = fma2(x2, fma2(pk(-1.0f / 3.0f, -1.0f / 3.0f), x, pk(1.2f, 1.2f)),
+                         fma2(pk(-1.5f, -1.5f), x, pk(2.0f / 3.0f, 2.0f / 3.0f)));
+    const f2 s_out = mul2(c, fma2(xi3, pk(-1.0f / 480.0f, -1.0f / 480.0f), poly));
+    // ce (2.4 - x - 1.5 / x + x^-5 / 160)
+    const f2 d_out = mul2(cc, fma2(mul2(xi3, xi2), pk(1.0f / 160.0f, 1.0f / 160.0f),
+                                   fma2(pk(-1.5f, -1.5f), xi, add2(pk(2.4f, 2.4f), mul2(x, pk(-1.0f, -1.0f))))));
+    float ia, ib, oa, ob, dia, dib, doa, dob;
+    upk(s_in, ia, ib);
+    upk(s_out, oa, ob);
+    upk(d_in, dia, dib);
+    upk(d_out, doa, dob);
+    s3 = pk(xa < 0.5f ? ia : oa, xb < 0.5f ? ib : ob);
+    ds = pk(xa < 0.5f ? dia : doa, xb < 0.5f ? dib : dob);
+  } else {  // Plummer
+    float pa, pb;
+    upk(add2(r2, pk(f.eps2_f, f.eps2_f)), pa, pb);
+    const f2 p = pk(rsqrt_approx(pa), rsqrt_approx(pb));
+    const f2 p2 = mul2(p, p);
+    s3 = mul2(p2, p);
+    ds = mul2(mul2(s3, p2), pk(-3.0f, -3.0f));
+  }
+  const float kd = -f.hscale_f * f.inv2xs_f * f.inv2xs_f;
+  D = fma2(hd, pk(kd, kd), ds);
+  return fma2(h, pk(-f.hscale_f, -f.hscale_f), s3);
+}
+
 // ---------------------------------------------------------------- FP64 ----
 
 template <int SOFT, bool VJP>
