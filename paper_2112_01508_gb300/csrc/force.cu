@@ -1102,9 +1102,10 @@ struct SymVjpSmem : SymSmem {
   float2 vz[kWarp];
 };
 
-// 5 resident blocks of 4 warps per SM (96 registers, a few bytes of spills): with the
-// cp.async staging measured best on the 128^3 set (1.490 ms against 1.518 with 4
-// blocks and 128 registers).
+// Resident blocks of 4 warps per SM: the forward at 8 (64 registers, no spills;
+// with the close pairs evaluated in the step it is 7% faster than at 5 on the
+// 128^3 set), the adjoint at 6 (80 registers; its softened branch with the
+// derivative spills beyond).
 #ifndef P3M_SYM_SOFT_INLINE
 #define P3M_SYM_SOFT_INLINE 1  // forward close pairs: 1 = packed softened form in the step (5-8% faster), 0 = queue
 #endif
@@ -1113,7 +1114,10 @@ struct SymVjpSmem : SymSmem {
 #endif
 constexpr int kSymUnroll = P3M_SYM_UNROLL;
 #ifndef P3M_SYM_MINBLOCKS
-#define P3M_SYM_MINBLOCKS 5
+#define P3M_SYM_MINBLOCKS 8
+#endif
+#ifndef P3M_SYMV_MINBLOCKS
+#define P3M_SYMV_MINBLOCKS 6  // the adjoint instance
 #endif
 
 __device__ __forceinline__ f2 shfl2(f2 v, int src) {
@@ -1131,7 +1135,7 @@ __device__ __forceinline__ f2 shfl_xor2(f2 v, int o) {
 // v the masked abar, is antisymmetric in (i, j) like the force, so the partner
 // receives the negated term; every particle is a receiver.
 template <int SOFT, bool VJP = false>
-__global__ void __launch_bounds__(kPThreads, P3M_SYM_MINBLOCKS) k_force_sym(TraversalArgs a, float4* __restrict__ acc4) {
+__global__ void __launch_bounds__(kPThreads, VJP ? P3M_SYMV_MINBLOCKS : P3M_SYM_MINBLOCKS) k_force_sym(TraversalArgs a, float4* __restrict__ acc4) {
   using Smem = typename std::conditional<VJP, SymVjpSmem, SymSmem>::type;
   __shared__ Smem smem[kPWarps];
   const unsigned full = 0xffffffffu;
