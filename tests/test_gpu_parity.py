@@ -264,3 +264,36 @@ def test_fp32_symmetric_matches_gather_and_oracle(n32k, case):
     # Newton's third law: the net force vanishes up to FP32 rounding of the sums
     net = np.abs(rs["acc"].sum(axis=1)).max()
     assert net <= 1e-6 * np.abs(rs["acc"]).sum(axis=1).max()
+
+
+@pytest.mark.parametrize("softening", ["plummer", "bspline"])
+def test_close_pairs_on_every_fp32_path(softening):
+    """Pairs closer than r_sw = 2.8 eps take the softened form (Section 2.1.1); on
+    every FP32 path one packed evaluation serves both halves of a step, each half
+    selecting its form (for the B-spline, its inner or outer piece).  A dense core in
+    which a large share of the interacting pairs is that close, on the each-pair-once
+    kernel, the one-sided kernel with all receivers active, and the one-sided kernel
+    on a partial receiver set, against the oracle."""
+    rng = np.random.default_rng(31)
+    x_r, eps = 0.1, 0.004
+    x_s, r_sw = x_r / 4.5, 2.8 * eps
+    core = 0.5 + 0.006 * rng.standard_normal((3, 3000))
+    pos = np.ascontiguousarray(np.mod(np.concatenate([core, rng.random((3, 3000))], axis=1), 1.0))
+    n = pos.shape[1]
+    G_m = 1.0 / n
+    d = np.sqrt(((core[:, :400, None] - core[:, None, :]) ** 2).sum(axis=0))
+    close = ((d > 0) & (d < r_sw)).sum() / ((d > 0) & (d < x_r)).sum()
+    assert close > 0.2  # the softened form is a large part of the work, both pieces in use
+    assert ((d > 0) & (d < 0.5 * 2.8 * eps)).any() and ((d > 0.5 * 2.8 * eps) & (d < r_sw)).any()
+    ref, pairs = oracle.sr_accel(pos, x_s, x_r, G_m, softening, eps)
+    for symmetric in (True, False):
+        r = gpu_forces(pos, x_s, x_r, G_m, softening, eps, precision=32, symmetric=symmetric)
+        assert np.isfinite(r["acc"]).all()
+        assert abs(r["pairs"] - pairs) <= max(2, 1e-6 * pairs)
+        assert rel_rms(r["acc"], ref) <= FP32_TOL
+    rung = synth.uniform_int8(n, 41, 0, 8)
+    ref_p, _ = oracle.sr_accel(pos, x_s, x_r, G_m, softening, eps, rung=rung, rung_min=4)
+    act = rung >= 4
+    r = gpu_forces(pos, x_s, x_r, G_m, softening, eps, precision=32, rung=rung, rung_min=4)
+    assert np.all(np.isnan(r["acc"][:, ~act]))
+    assert rel_rms(r["acc"][:, act], ref_p[:, act]) <= FP32_TOL

@@ -254,21 +254,27 @@ def test_vjp_each_pair_once_matches_one_sided(rung_min):
 
 @pytest.mark.parametrize("softening", ["plummer", "bspline"])
 def test_vjp_dense_cluster_with_coincident_particles(softening):
-    """FP32 adjoint on a dense cluster in which most pairs are closer than r_sw (the
-    close-pair queue overflows within a step) and 40 particles sit exactly on others
-    (r = 0: the softened B(0) acts on abar_i - abar_j), against the oracle."""
+    """FP32 adjoint on a dense cluster in which most pairs are closer than r_sw (most
+    steps take the packed softened branch with its derivative) and 40 particles sit
+    exactly on others (r = 0: the softened B(0) acts on abar_i - abar_j), against the
+    oracle: the each-pair-once and the one-sided kernels, with every particle active
+    and on a partial set (abar masked to the receivers)."""
     rng = np.random.default_rng(23)
     x_r, eps = 0.1, 0.004
     dense = 0.4 + 2e-3 * rng.normal(size=(3, 1500))
     pos = np.concatenate([dense, rng.random((3, 1000)), dense[:, :40]], axis=1) % 1.0
     n = pos.shape[1]
     abar = rng.normal(size=(3, n))
-    ref = oracle.sr_vjp(pos, abar, x_r / 4.5, x_r, 1.0 / n, softening, eps)
-    with ShortRange(n, x_r / 4.5, x_r, 1.0 / n, softening=softening, eps=eps) as sr:
-        p = torch.from_numpy(pos.copy()).cuda()
-        sr.sort(p)
-        sr.build_pairs()
-        ab = sr.permute(torch.from_numpy(abar).cuda().float().contiguous())
-        xb = sr.unpermute(sr.vjp(p, ab, 32)).double().cpu().numpy()
-    assert np.isfinite(xb).all()
-    assert rel_rms(xb, ref) <= 1e-5, rel_rms(xb, ref)
+    rung = synth.uniform_int8(n, 29, 0, 8)
+    for symmetric, rung_min in ((True, None), (False, None), (True, 5), (False, 5)):
+        ref = oracle.sr_vjp(pos, abar, x_r / 4.5, x_r, 1.0 / n, softening, eps,
+                            rung=rung if rung_min else None, rung_min=rung_min or 0)
+        with ShortRange(n, x_r / 4.5, x_r, 1.0 / n, softening=softening, eps=eps, symmetric=symmetric) as sr:
+            p = torch.from_numpy(pos.copy()).cuda()
+            rg = torch.from_numpy(rung.copy()).cuda() if rung_min else None
+            sr.sort(p, carry=[rg] if rg is not None else [])
+            sr.build_pairs(rg, rung_min or 0)
+            ab = sr.permute(torch.from_numpy(abar).cuda().float().contiguous())
+            xb = sr.unpermute(sr.vjp(p, ab, 32)).double().cpu().numpy()
+        assert np.isfinite(xb).all()
+        assert rel_rms(xb, ref) <= 1e-5, (symmetric, rung_min, rel_rms(xb, ref))
