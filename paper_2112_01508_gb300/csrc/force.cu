@@ -1072,8 +1072,10 @@ __global__ void k_parts_finish(TraversalArgs a) {
 // sums are reduced and added, like the receivers' own sums at the end of the
 // chunk, into an FP32 float4 array with vector atomics.  k_sym_finish scales
 // that array into the caller's 3 x n output.  Pairs closer than r_sw (the
-// softened form) leave the step's sums: they are queued per warp and evaluated
-// 32 at a time, one per lane, their terms added to both particles directly.
+// softened form) are evaluated in the step: when some lane holds one, one packed
+// softened evaluation serves both halves and each half selects its form
+// (P3M_SYM_SOFT_INLINE; 0 builds the earlier variant, which queues them per warp
+// and evaluates them 32 at a time, one per lane, with atomics to both particles).
 // ---------------------------------------------------------------------------
 
 constexpr float kSymPad = 1e10f;  // padding supplier at -1e10, invalid receiver at +1e10: finite B, no hit
@@ -1297,9 +1299,9 @@ __global__ void __launch_bounds__(kPThreads, VJP ? P3M_SYMV_MINBLOCKS : P3M_SYM_
             f2 B = bracket_main_f32x2<SOFT>(r2, a.f);
             // Pairs closer than r_sw (the softened form): a cheap vote first, the
             // exact condition (a hit, not a zero displacement) only when some pair
-            // is that close.  Such pairs leave the step's sums and go to a queue
-            // that is evaluated 32 at a time, one per lane, so that the long
-            // softened branch runs with full warps.
+            // is that close; then one packed softened evaluation for both halves
+            // (or, in the queue variant, the pairs leave the step's sums for a
+            // queue evaluated 32 at a time, one per lane).
             if (kCheckSoft && __any_sync(full, fminf(q0, q1) < a.f.rsw2_f)) {
               const bool rare0 = c0 > 0.f && q0 < a.f.rsw2_f && q0 > kR2Self;
               const bool rare1 = c1 > 0.f && q1 < a.f.rsw2_f && q1 > kR2Self;
@@ -1357,8 +1359,9 @@ __global__ void __launch_bounds__(kPThreads, VJP ? P3M_SYMV_MINBLOCKS : P3M_SYM_
             const f2 vz2 = add2(viz, pk(wz.x, wz.y));
             f2 D;
             f2 B = bracket_main_vjp_f32x2<SOFT>(r2, a.f, D);
-            // close pairs (r < r_sw, coincident ones included) to the queue, as in
-            // the forward; selects, since the main branch is not finite at r = 0
+            // close pairs (r < r_sw, coincident ones included) as in the forward, B and
+            // B'/r of the softened form; selects, since the main branch is not finite
+            // at r = 0
             if (kCheckSoft && __any_sync(full, fminf(q0, q1) < a.f.rsw2_f)) {
               const bool rare0 = c0 > 0.f && q0 < a.f.rsw2_f;
               const bool rare1 = c1 > 0.f && q1 < a.f.rsw2_f;
