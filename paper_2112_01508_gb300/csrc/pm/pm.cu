@@ -75,15 +75,27 @@ __device__ __forceinline__ T weight(T t) {
 template <int P, class T>
 __device__ __forceinline__ long long stencil_1d(double s, T (&w)[P]) {
   const double c = (P & 1) ? floor(s + 0.5) : floor(s);
-  const long long first = (long long)c - ((P & 1) ? (P - 1) / 2 : P / 2 - 1);
+  constexpr int off = (P & 1) ? (P - 1) / 2 : P / 2 - 1;
+  const long long first = (long long)c - off;
+  // cell first + a lies at (a - off) - f from the particle, f = s - c (exact in FP64):
+  // one FP64 subtraction per coordinate, the weights in T
+  const T f = (T)(s - c);
 #pragma unroll
-  for (int a = 0; a < P; ++a) w[a] = weight<P, T>((T)fabs((double)(first + a) - s));
+  for (int a = 0; a < P; ++a) {
+    const T d = (T)(a - off) - f;
+    w[a] = weight<P, T>(d < T(0) ? -d : d);
+  }
   return first;
 }
 
+// m mod n for -n <= m < 2n: every stencil index lies within 8 cells of the mesh
+// (first cell >= -6, last <= n + 6), and n_phi >= 8.
 __device__ __forceinline__ int wrap(long long m, long long n) {
-  long long r = m % n;
-  return (int)(r < 0 ? r + n : r);
+  int r = (int)m;
+  const int nn = (int)n;
+  r += r < 0 ? nn : 0;
+  r -= r >= nn ? nn : 0;
+  return r;
 }
 
 __device__ __forceinline__ bool position_ok(double x, double box) { return x >= 0.0 && x < box; }
