@@ -579,7 +579,7 @@ __device__ __forceinline__ void enumerate_suppliers_once(const TraversalArgs& a,
       take = candidate_range<Real>(a, rc, F, cb + lane, ncand, clip_from, start, cnt, dpk);
       tm = __ballot_sync(full, take);
       if (tm == 0) continue;
-      if (nlist + __popc(tm) > kListCap) {  // flush first; this round is appended after
+      if (nlist + __popc(tm) > kListCap) {  // flush first; this batch of candidates is appended after
         overflow = true;
         break;
       }
