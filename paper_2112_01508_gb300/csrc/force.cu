@@ -1111,6 +1111,9 @@ struct SymVjpSmem : SymSmem {
 #ifndef P3M_SYM_SOFT_INLINE
 #define P3M_SYM_SOFT_INLINE 1  // forward close pairs: 1 = packed softened form in the step (5-8% faster), 0 = queue
 #endif
+#ifndef P3M_SYM_OWN_TRIANGLE
+#define P3M_SYM_OWN_TRIANGLE 1  // forward: the chunk's own pairs in a triangular pass, not staged
+#endif
 #ifndef P3M_SYM_UNROLL
 #define P3M_SYM_UNROLL 1  // rotation steps per loop iteration
 #endif
@@ -1450,11 +1453,49 @@ __global__ void __launch_bounds__(kPThreads, VJP ? P3M_SYMV_MINBLOCKS : P3M_SYM_
       __syncwarp();
     };
 
+    // The chunk's own pairs (forward): lane l with lane l + k, k = 1 ... 16 (k = 16 from
+    // the lower half only), each pair {i, j} of the chunk once; the partner's share
+    // comes back by a shuffle from lane l - k.  The staged suppliers then start after
+    // the chunk, so no block needs the j > i mask.
+    constexpr bool kOwnTri = !VJP && P3M_SYM_OWN_TRIANGLE;
+    if constexpr (kOwnTri) {
+      float ox = 0.f, oy = 0.f, oz = 0.f, oh = 0.f;
+#pragma unroll 1
+      for (int k = 1; k <= kWarp / 2; ++k) {
+        const int m = (lane + k) & (kWarp - 1);
+        const float xm = __shfl_sync(full, rx, m), ym = __shfl_sync(full, ry, m), zm = __shfl_sync(full, rz, m);
+        const bool vm = __shfl_sync(full, (int)F.valid, m) != 0;
+        const bool take = F.valid && vm && (k < kWarp / 2 || lane < kWarp / 2);
+        const float dx = rx - xm, dy = ry - ym, dz = rz - zm;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kR2Floor)));
+        const float c = take ? fma_sat(r2, -kCutScale, xr2s) : 0.f;
+        oh += c;
+        float Dm;
+        float B = bracket_main_f32<SOFT, false>(r2, a.f, Dm);
+        const bool rare = c > 0.f && r2 < a.f.rsw2_f && r2 > kR2Self;
+        if (__any_sync(full, rare)) {
+          float Ds;
+          const float Bs = bracket_soft_f32<SOFT, false>(r2, a.f, a.sc, Ds);
+          if (rare) B = Bs;
+        }
+        B = c > 0.f ? B : 0.f;  // a select: padded lanes may carry a non-finite B
+        const float tx = B * dx, ty = B * dy, tz = B * dz;
+        const int from = (lane - k) & (kWarp - 1);
+        ox += tx - __shfl_sync(full, tx, from);
+        oy += ty - __shfl_sync(full, ty, from);
+        oz += tz - __shfl_sync(full, tz, from);
+      }
+      ax = add2(ax, pk(ox, 0.f));
+      ay = add2(ay, pk(oy, 0.f));
+      az = add2(az, pk(oz, 0.f));
+      hitsf = add2(hitsf, pk(oh, 0.f));
+    }
+
     // Stage the survivors of each batch of 32 list positions; evaluate a block
     // whenever 64 are staged, and the rest once the enumeration is done (one
     // call site of eval_block, so its loops are inlined once).
     enumerate_suppliers_once<float>(
-        a, rc, F, S.L, lane, ch.start,
+        a, rc, F, S.L, lane, kOwnTri ? c_end : ch.start,
         [&](int nlist, int total, bool last) {
           const WarpList& L = S.L;
           int e_cur = 0;  // list entry holding position b (as in k_force_packed)
